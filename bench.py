@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark of the far-field radiation sum: amplitude updates per second.
+
+One step = one rad_accumulate call over one time step of the LWFA-shaped bunch
+(1e5 macro-particles, 512 log-spaced frequencies 1e14..1e20 rad/s, 16 x 16
+directions within +-10 mrad, Gaussian form factor sigma = 0.1 um): 1.34e10
+amplitude updates (particle x omega x n).  Inputs are synthetic, resident in HBM
+before the timed region, and distinct per step (a ring of 64 steps x 8 MB =
+512 MB, larger than L2).  Prints one JSON line.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (a bounded sample
+of bins per step); N > 1 under torchrun runs one independent job per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "amplitude updates/s (particle×ω×n×step) at ≤1e-5 rel err; p50/p99 job latency"
+UNIT = "updates/s"
+SM_MAX_MHZ = 2070.0
+MUFU_PER_CLK_SM = 16.0   # sin/cos lane-ops per clock per SM (measured by rad_probe_peaks)
+MUFU_PER_UPDATE = 2.0    # one sin and one cos per (particle, omega, n)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "accumulate_lwfa_traffic.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_1802_03972_gb300", "csrc", "rad_kernels.cu")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--ring", type=int, default=64)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="keep the default tile instead of rad_tune")
+    p.add_argument("--peaks", action="store_true", help="also run the pipe-throughput probe")
+    return p.parse_args()
+
+
+def config(wl, extra=None):
+    c = {"workload": "lwfa_bunch (1e5 macro-particles, 512 log omega 1e14-1e20 rad/s, "
+                     "16x16 directions +-10 mrad, Gaussian form factor 0.1 um)",
+         "n_particles": wl.n_particles, "n_omega": int(wl.omega.shape[0]),
+         "n_dir": int(wl.dirs.shape[0]), "updates_per_step": wl.updates_per_step(),
+         "l2": "inputs larger than L2: distinct per-step particle arrays, ring of 64 x 8 MB"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_hash() -> str:
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def traffic_per_launch(updates_per_step: int):
+    """DRAM bytes per accumulate launch from the committed ncu summary, scaled to this
+    launch's updates; None when the kernel source changed since the capture."""
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_sha") != kernel_hash():
+        return None
+    return t["dram_bytes_per_launch"] * updates_per_step / t["updates_per_launch"]
+
+
+def cpu_oracle_rate(wl, n_bins: int, target_s: float):
+    """Oracle (as it stands) on n_bins sampled bins x all particles, steps until
+    about target_s of CPU work: returns (updates/s, threads, description, steps)."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(123)
+    bins = [(int(rng.integers(0, wl.dirs.shape[0])), int(rng.integers(0, wl.omega.shape[0])))
+            for _ in range(n_bins)]
+    bo, bd = oracle.grid_bins(wl.omega, wl.dirs, bins)
+    acc = oracle.Accumulator(bo, bd, wl.ff_kind, wl.ff_width)
+    st = wl.step(0)
+    t0 = time.perf_counter()
+    acc.accumulate(st.r, st.beta, st.beta_dot, st.w, st.t, st.dt)
+    t1 = time.perf_counter() - t0
+    steps = max(1, min(200, int(round(target_s / max(t1, 1e-6)))))
+    data = [wl.step(s) for s in range(1, steps + 1)]
+    t0 = time.perf_counter()
+    for st in data:
+        acc.accumulate(st.r, st.beta, st.beta_dot, st.w, st.t, st.dt)
+    el = time.perf_counter() - t0
+    upd = n_bins * wl.n_particles * steps
+    desc = (f"{n_bins} sampled (direction, omega) bins x {wl.n_particles} macro-particles x "
+            f"{steps} steps = {upd:.3g} updates in {el:.1f} s")
+    return upd / el, oracle.num_threads(), desc, steps
+
+
+def reference_arm(args, wl):
+    """FP64 CPU oracle, a bounded sample of bins per step, rank 0 only."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(7)
+    # bins per step so that one step takes ~0.3 s
+    probe = [(int(rng.integers(0, 256)), int(rng.integers(0, 512))) for _ in range(16)]
+    bo, bd = oracle.grid_bins(wl.omega, wl.dirs, probe)
+    acc = oracle.Accumulator(bo, bd, wl.ff_kind, wl.ff_width)
+    st = wl.step(0)
+    t0 = time.perf_counter()
+    acc.accumulate(st.r, st.beta, st.beta_dot, st.w, st.t, st.dt)
+    per_bin = (time.perf_counter() - t0) / 16
+    n_bins = int(max(16, min(4096, 0.3 / max(per_bin, 1e-9))))
+    bins = [(int(rng.integers(0, 256)), int(rng.integers(0, 512))) for _ in range(n_bins)]
+    bo, bd = oracle.grid_bins(wl.omega, wl.dirs, bins)
+    acc = oracle.Accumulator(bo, bd, wl.ff_kind, wl.ff_width)
+    data = [wl.step(s % 64) for s in range(min(64, args.steps + args.warmup))]
+    for s in range(args.warmup):
+        st = data[s % len(data)]
+        acc.accumulate(st.r, st.beta, st.beta_dot, st.w, st.t, st.dt)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        st = data[(args.warmup + s) % len(data)]
+        acc.accumulate(st.r, st.beta, st.beta_dot, st.w, st.t, st.dt)
+    el = time.perf_counter() - t0
+    upd = n_bins * wl.n_particles * args.steps
+    value = upd / el
+    sample = (f"each step: {n_bins} sampled (direction, omega) bins x {wl.n_particles} "
+              f"macro-particles of the LWFA-shaped bunch")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config(wl, {"bins_per_step": n_bins}),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1802_03972_gb300 import inputs
+    wl = inputs.lwfa_bunch(seed=2 + rank)
+    if args.impl == "reference":
+        if rank == 0:
+            reference_arm(args, wl)
+        return
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1802_03972_gb300 import build, rad
+    build.build()
+    rad.load()
+    dev = torch.device("cuda", local)
+
+    # Resident inputs: a ring of distinct steps.
+    ring = max(1, min(args.ring, args.steps + args.warmup))
+    steps_host = [wl.step(s) for s in range(ring)]
+    ring_dev = [[torch.from_numpy(a).to(dev) for a in (st.r, st.beta, st.beta_dot, st.w)]
+                for st in steps_host]
+    upd = wl.updates_per_step()
+    ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
+    tile = ctx.tune(wl.n_particles) if not args.no_tune else ctx.get_tile()
+
+    def run(k):
+        st = steps_host[k % ring]
+        ctx.accumulate(*ring_dev[k % ring], st.t + (k // ring) * ring * st.dt, st.dt)
+
+    for k in range(args.warmup):
+        run(k)
+    ctx.sync()
+    ctx.reset()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    time.sleep(0.3)
+    launches0 = rad.kernel_launch_count()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        run(k)
+    e1.record()
+    torch.cuda.synchronize()
+    elapsed_ms = e0.elapsed_time(e1)
+    clocks = clk.stop()
+    launches = rad.kernel_launch_count() - launches0
+    pre_ms, acc_ms, calls = ctx.profile_read()
+    ctx.profile(False)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        dist.barrier()
+    value = world * args.steps * upd / (elapsed_ms / 1e3)
+
+    # Parity of the timed configuration (tile choice included) on two sampled
+    # directions x all frequencies: the per-direction relative spectral error.
+    rel_err = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        chk = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
+        chk.set_tile(*ctx.get_tile())
+        rows = [5, 200]
+        n_om = wl.omega.shape[0]
+        bins = [(d, o) for d in rows for o in range(n_om)]
+        bo, bd = oracle.grid_bins(wl.omega, wl.dirs, bins)
+        acc = oracle.Accumulator(bo, bd, wl.ff_kind, wl.ff_width)
+        for k in range(2):
+            st = steps_host[k]
+            chk.accumulate(*ring_dev[k], st.t, st.dt)
+            acc.accumulate(st.r, st.beta, st.beta_dot, st.w, st.t, st.dt)
+        tot = chk.spectrum()[2]
+        ref = acc.spectra()["tot"].reshape(len(rows), n_om)
+        rel_err = max(float(np.linalg.norm(tot[d] - r) / np.linalg.norm(r)) for d, r in zip(rows, ref))
+        chk.close()
+
+    # Roofline of the accumulate kernel (MUFU-bound: 2 sin/cos per update).
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    acc_s = acc_ms / max(calls, 1) / 1e3
+    achieved = upd / acc_s if acc_s > 0 else None
+    peak = sm * MUFU_PER_CLK_SM * SM_MAX_MHZ * 1e6 / MUFU_PER_UPDATE
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
+            "frac": achieved / peak if achieved else None, "traffic": traffic_per_launch(upd),
+            "kernel": "accumulate_kernel variant %d (%s), omega tile %d, chunk %s" % (
+                tile[0], {0: "256 threads x 2 omega", 1: "256 x 4", 2: "128 x 2"}[tile[0]], tile[1],
+                tile[2] or "auto"),
+            "peak_basis": f"{sm} SMs x {MUFU_PER_CLK_SM:g} MUFU sin/cos per clk x {SM_MAX_MHZ:g} MHz "
+                          f"(max SM clock) / {MUFU_PER_UPDATE:g} per update",
+            "prepass_ms_per_step": pre_ms / max(calls, 1),
+            "accumulate_ms_per_step": acc_ms / max(calls, 1)}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
+
+    # End to end through the C ABI with pinned host buffers: H2D of each step's
+    # particles inside rad_accumulate, D2H of the spectra by rad_spectrum.
+    e2e = None
+    if not args.no_e2e:
+        n_e2e = min(args.steps, 20)
+        pinned = []
+        for st in steps_host[:min(ring, 8)]:
+            pinned.append([torch.from_numpy(a).pin_memory() for a in (st.r, st.beta, st.beta_dot, st.w)])
+        outs = [np.zeros((wl.dirs.shape[0], wl.omega.shape[0])) for _ in range(3)]
+        ectx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
+        ectx.accumulate(*pinned[0], steps_host[0].t, steps_host[0].dt)
+        ectx.spectrum(out=outs)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(n_e2e):
+            st = steps_host[k % len(pinned)]
+            ectx.accumulate(*pinned[k % len(pinned)], st.t, st.dt)
+            ectx.spectrum(out=outs)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * n_e2e * upd / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(a.numel() * 8 for a in pinned[0])),
+               "d2h_bytes_per_step": int(sum(o.nbytes for o in outs)), "steps": n_e2e}
+        ectx.close()
+
+    # The plain FP64 GPU kernel on the same GPU (2 steps).
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        c64 = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width, prec=rad.PREC_FP64)
+        st = steps_host[0]
+        c64.accumulate(*ring_dev[0], st.t, st.dt)
+        c64.sync()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for k in range(2):
+            st = steps_host[k + 1]
+            c64.accumulate(*ring_dev[k + 1], st.t, st.dt)
+        f1.record()
+        torch.cuda.synchronize()
+        v64 = 2 * upd / (f0.elapsed_time(f1) / 1e3)
+        fp64 = {"value": v64, "unit": UNIT, "steps": 2, "mixed_over_fp64": value / world / v64}
+        c64.close()
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        rate, cores, desc, _ = cpu_oracle_rate(wl, 64, 10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    peaks = None
+    if args.peaks and rank == 0:
+        p = rad.probe_peaks()
+        peaks = {"ffma_lanes_per_clk_sm": p[0], "ffma2_lanes_per_clk_sm": p[2],
+                 "mufu_per_clk_sm": p[4], "dfma_per_clk_sm": p[6], "probe_mhz": p[5]}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(wl),
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clocks, "rel_err_sampled": rel_err, "fp64_plain": fp64}
+        if peaks:
+            out["peaks"] = peaks
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

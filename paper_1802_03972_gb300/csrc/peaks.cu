@@ -1,0 +1,250 @@
+// Pipe-throughput microbenchmarks for the roofline denominators of the
+// radiation kernel: FP32 FMA (scalar and packed f32x2), MUFU sin/cos, FP64
+// FMA, float rounding and f64<->f32 conversion, and one mixed loop with the
+// op mix of the phase-accumulate inner loop (2 MUFU + packed FMAs).
+//
+// Each kernel runs independent dependency chains per thread so the pipe, not
+// latency, limits it; a block records its start/end SM cycle counter, so the
+// rates come out per SM clock cycle, independent of the clock the GPU ran at.
+// Entry point: rad_probe_peaks() (C ABI), results in lane-ops / clk / SM.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace {
+
+constexpr int kThreads = 512;
+
+__device__ __forceinline__ void stamp(long long* cyc, long long t0) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cyc[2 * blockIdx.x] = t0;
+    cyc[2 * blockIdx.x + 1] = clock64();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_ffma(float* out, long long* cyc, int iters, float a, float b) {
+  long long t0 = clock64();
+  float x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * 1e-3f + i;
+#pragma unroll 2
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fmaf(x[i], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+  stamp(cyc, t0);
+}
+
+__global__ void __launch_bounds__(kThreads) k_ffma2(float* out, long long* cyc, int iters, float a, float b) {
+  long long t0 = clock64();
+  float2 x[8];
+  const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = make_float2(threadIdx.x * 1e-3f + i, i * 0.5f);
+#pragma unroll 2
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = __ffma2_rn(x[i], a2, b2);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i].x + x[i].y;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+  stamp(cyc, t0);
+}
+
+__device__ __forceinline__ float sin_approx(float x) {
+  float y;
+  asm volatile("sin.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+  float y;
+  asm volatile("cos.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__global__ void __launch_bounds__(kThreads) k_mufu(float* out, long long* cyc, int iters) {
+  long long t0 = clock64();
+  float x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * 1e-3f + i * 0.1f;
+#pragma unroll 2
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+      x[i] = sin_approx(x[i]);
+      x[i + 1] = cos_approx(x[i + 1]);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+  stamp(cyc, t0);
+}
+
+__global__ void __launch_bounds__(kThreads) k_dfma(float* out, long long* cyc, int iters, double a, double b) {
+  long long t0 = clock64();
+  double x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * 1e-3 + i;
+#pragma unroll 2
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
+  stamp(cyc, t0);
+}
+
+__global__ void __launch_bounds__(kThreads) k_frnd(float* out, long long* cyc, int iters, float a) {
+  long long t0 = clock64();
+  float x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * 1.3e-3f + i * 0.7f;
+#pragma unroll 2
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float r;
+      asm volatile("cvt.rni.f32.f32 %0, %1;" : "=f"(r) : "f"(x[i]));
+      x[i] = r + a;  // one FADD per round so the chain stays live
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+  stamp(cyc, t0);
+}
+
+__global__ void __launch_bounds__(kThreads) k_cvt(float* out, long long* cyc, int iters) {
+  long long t0 = clock64();
+  double x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * 1e-3 + i;
+#pragma unroll 2
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float f = __double2float_rn(x[i]);   // cvt f64 -> f32
+      x[i] = (double)(f * 1.0000001f);     // cvt f32 -> f64 (+1 FMUL)
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
+  stamp(cyc, t0);
+}
+
+// Mixed loop shaped like the phase-accumulate inner loop for one packed pair
+// of frequencies: 2 sin + 2 cos MUFU ops and NF packed FMAs per iteration.
+template <int NF>
+__global__ void __launch_bounds__(kThreads) k_mix(float* out, long long* cyc, int iters, float a) {
+  long long t0 = clock64();
+  float2 acc[NF];
+  float2 ph = make_float2(threadIdx.x * 1e-3f, threadIdx.x * 2e-3f);
+  const float2 a2 = make_float2(a, a);
+#pragma unroll
+  for (int i = 0; i < NF; ++i) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int it = 0; it < iters; ++it) {
+    float2 c = make_float2(cos_approx(ph.x), cos_approx(ph.y));
+    float2 s = make_float2(sin_approx(ph.x), sin_approx(ph.y));
+#pragma unroll
+    for (int i = 0; i < NF; i += 2) {
+      acc[i] = __ffma2_rn(a2, c, acc[i]);
+      acc[i + 1] = __ffma2_rn(a2, s, acc[i + 1]);
+    }
+    ph = __ffma2_rn(ph, a2, c);
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int i = 0; i < NF; ++i) t += acc[i].x + acc[i].y;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
+  stamp(cyc, t0);
+}
+
+}  // namespace
+
+extern "C" {
+
+// Runs every probe once (after one warm-up launch each) on the current device.
+// out[] receives, per probe, lane-ops per SM clock cycle, then the effective SM
+// clock in MHz seen by that probe:
+//   [0,1] FFMA scalar      [2,3] FFMA2 (lane-ops = 2 per lane per instr)
+//   [4,5] MUFU sin/cos     [6,7] DFMA
+//   [8,9] FRND (+1 FADD)   [10,11] cvt f64->f32->f64 pairs (2 cvt per step)
+//   [12,13] mixed, MUFU ops/clk/SM with 8 FFMA2 per 4 MUFU
+//   [14,15] mixed, MUFU ops/clk/SM with 16 FFMA2 per 4 MUFU
+// Returns 0 on success, otherwise the CUDA error code. n_out must be >= 16.
+int rad_probe_peaks(double* out, int n_out) {
+  if (out == nullptr || n_out < 16) return (int)cudaErrorInvalidValue;
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  // Every probe launches exactly one wave: n_sm x (its resident blocks per SM).
+  const int max_per_sm = 2048 / kThreads;
+  const int blocks = n_sm * max_per_sm;
+  float* d_out = nullptr;
+  long long* d_cyc = nullptr;
+  cudaError_t e = cudaMalloc(&d_out, sizeof(float) * blocks * kThreads);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaMalloc(&d_cyc, sizeof(long long) * 2 * blocks);
+  if (e != cudaSuccess) { cudaFree(d_out); return (int)e; }
+  long long* h_cyc = new long long[2 * blocks];
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+
+  auto measure = [&](const void* kern, auto launch, double ops_per_thread, double* res) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > max_per_sm) per_sm = max_per_sm;
+    const int nb = n_sm * per_sm;
+    launch(nb);  // warm-up
+    cudaEventRecord(ev0);
+    launch(nb);
+    cudaEventRecord(ev1);
+    cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaMemcpy(h_cyc, d_cyc, sizeof(long long) * 2 * nb, cudaMemcpyDeviceToHost);
+    double cyc_sum = 0.0;
+    for (int b = 0; b < nb; ++b) cyc_sum += (double)(h_cyc[2 * b + 1] - h_cyc[2 * b]);
+    const double cyc_mean = cyc_sum / nb;
+    const double ops_per_sm = ops_per_thread * kThreads * per_sm;
+    res[0] = ops_per_sm / cyc_mean;
+    res[1] = cyc_mean / (ms * 1e-3) / 1e6;
+  };
+
+  const int it = 1 << 14;
+  measure((const void*)k_ffma, [&](int nb) { k_ffma<<<nb, kThreads>>>(d_out, d_cyc, it, 0.999f, 1e-3f); }, 8.0 * it, out + 0);
+  measure((const void*)k_ffma2, [&](int nb) { k_ffma2<<<nb, kThreads>>>(d_out, d_cyc, it, 0.999f, 1e-3f); }, 16.0 * it, out + 2);
+  measure((const void*)k_mufu, [&](int nb) { k_mufu<<<nb, kThreads>>>(d_out, d_cyc, it / 4); }, 8.0 * (it / 4), out + 4);
+  measure((const void*)k_dfma, [&](int nb) { k_dfma<<<nb, kThreads>>>(d_out, d_cyc, it / 16, 0.999, 1e-3); }, 8.0 * (it / 16), out + 6);
+  measure((const void*)k_frnd, [&](int nb) { k_frnd<<<nb, kThreads>>>(d_out, d_cyc, it / 4, 0.25f); }, 8.0 * (it / 4), out + 8);
+  measure((const void*)k_cvt, [&](int nb) { k_cvt<<<nb, kThreads>>>(d_out, d_cyc, it / 16); }, 16.0 * (it / 16), out + 10);
+  measure((const void*)k_mix<8>, [&](int nb) { k_mix<8><<<nb, kThreads>>>(d_out, d_cyc, it / 4, 0.999f); }, 4.0 * (it / 4), out + 12);
+  measure((const void*)k_mix<16>, [&](int nb) { k_mix<16><<<nb, kThreads>>>(d_out, d_cyc, it / 4, 0.999f); }, 4.0 * (it / 4), out + 14);
+
+  e = cudaGetLastError();
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  delete[] h_cyc;
+  cudaFree(d_out);
+  cudaFree(d_cyc);
+  return (int)e;
+}
+
+}  // extern "C"

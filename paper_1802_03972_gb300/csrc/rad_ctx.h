@@ -1,0 +1,59 @@
+// Host-side definition of a radiation context (opaque in the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "rad.h"
+#include "rad_impl.h"
+
+struct rad_ctx {
+  int n_omega = 0, n_dir = 0, n_bins = 0;
+  rad_ff ff{};
+  int prec = RAD_PREC_MIXED;
+  cudaStream_t stream = nullptr;
+  rad_tile tile{};
+  // device buffers
+  double* d_omega = nullptr;
+  double* d_om_turns = nullptr;
+  float* d_om_tab = nullptr;
+  double* d_dirs = nullptr;
+  float* d_dir_tab = nullptr;
+  double* d_ref = nullptr;
+  int* d_status = nullptr;
+  unsigned long long* d_counter = nullptr;
+  radimpl::JobStatic* d_js = nullptr;
+  double* d_spec = nullptr;      // [3][n_bins] readout staging for host outputs
+  float* d_state = nullptr;      // MIXED: [16][n_bins]
+  double* d_state64 = nullptr;   // FP64:  [12][n_bins]
+  unsigned* d_tile_cnt = nullptr;
+  int tile_cnt_cap = 0;
+  double* d_stage = nullptr;     // staging for host particle arrays
+  size_t stage_cap = 0;
+  radimpl::JobStatic h_js{};     // host mirror of d_js
+  // kernel timing (rad_profile_*): event triples around pre-pass / accumulate
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;  // 3 per timed call
+  size_t prof_used = 0;
+  long long generation = 0;      // bumped whenever d_js changes
+  rad_status last_err = RAD_OK;
+  bool failed = false;
+};
+
+namespace radimpl {
+
+rad_status fail(rad_ctx* c, rad_status s);
+rad_status cuda_check(rad_ctx* c, cudaError_t e);
+int default_omega_tile(int variant, int n_omega);
+bool valid_omega_tile(int variant, int wt);
+void fill_tiles(JobStatic& js, int variant, int wt);
+int resident_ctas(int variant);
+int auto_chunk_for(int variant, long long n, int n_tiles);
+int auto_chunk(const rad_ctx* c, int variant, long long n, int n_tiles);
+rad_status ensure_capacity(rad_ctx* c, long long n, int n_chunks);
+rad_status enqueue_accumulate(rad_ctx* c, long long n, const double* r, const double* beta,
+                              const double* bdot, const double* w, double t, double dt);
+rad_status upload_static(rad_ctx* c);
+
+}  // namespace radimpl

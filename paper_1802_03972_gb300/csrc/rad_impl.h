@@ -1,0 +1,114 @@
+// Internal declarations of the radiation library (not part of the C ABI).
+//
+// Data layout in HBM, per job (one rad_ctx):
+//   om_tab   float [4][n_omega]  omega/2pi as hi part, its negation, and the
+//                                hi/lo parts of omega (rad/s) for the phase
+//   om_turns double [n_omega]    omega / 2pi (turns per second)
+//   omega    double [n_omega]
+//   dir_tab  float [12][n_dir]   n hi, n lo, transverse basis e1, e2
+//   dirs     double [n_dir][3]
+//   state    float [16][n_bins]  8 compensated sums + 8 compensations:
+//                                U.e1 re/im, U.e2 re/im, V.e1 re/im, V.e2 re/im
+//   partials float [chunks][8][n_bins]   per-work-item partial sums of a call
+//   rec      float [20][n_cap]   per-particle records written by the pre-pass
+// Bins are row-major: bin = direction * n_omega + frequency.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "rad.h"
+
+namespace radimpl {
+
+constexpr int kRecFields = 20;
+constexpr int kComps = 8;
+constexpr int kDirTab = 12;
+constexpr int kOmTab = 4;
+// Work items hold a multiple of 256 macro-particles: a whole number of
+// shared-memory tiles (threads / directions-per-tile particles) for every
+// kernel variant and tile shape.
+constexpr int kChunkAlign = 256;
+
+// Device status bits (per job).
+enum : int { ST_BAD_PARTICLE = 1, ST_SLOW_PHASE = 2, ST_TIMEOUT = 4 };
+
+// Per-job data that does not change between calls.
+struct JobStatic {
+  int n_omega, n_dir, n_bins;
+  int wt, nt;                     // tile: wt frequencies x nt directions
+  int tiles_om, tiles_dir, n_tiles;
+  float tau_fast;                 // |delta tau| bound of the fast phase path, s
+  int chunk_cap;                  // capacity of partials, in chunks
+  long long n_cap;                // capacity of rec, in particles
+  const float* om_tab;
+  const double* om_turns;
+  const double* omega;
+  const float* dir_tab;
+  const double* dirs;
+  float* state;
+  float* partials;
+  unsigned* tile_cnt;             // [n_tiles] arrival counters (self-resetting)
+  float* rec;
+  double* ref;                    // [4]: reference position xyz, t (per call)
+  int* status;
+};
+
+// Per-call data of one job.
+struct JobCall {
+  long long n;
+  const double* r;
+  const double* beta;
+  const double* bdot;
+  const double* w;
+  double t, dt;
+  int ck;                // macro-particles per work item (multiple of kChunkAlign)
+  int n_chunks;
+  long long item_begin;  // first global work item of this job
+  int block_begin;       // first pre-pass block of this job
+  int pad_;
+};
+
+struct LaunchArgs {
+  const JobStatic* js;   // device [n_jobs]
+  const JobCall* jc;     // device [n_jobs] (unused when use_inline)
+  int n_jobs;
+  int use_inline;        // 1: single job, call passed by value below
+  long long n_items;
+  unsigned long long* item_counter;
+  JobCall inline_call;
+};
+
+// Kernel variants of the mixed-precision accumulate kernel.
+struct Variant {
+  int threads;
+  int w;  // frequencies per thread
+};
+constexpr int kNumVariants = 3;
+inline Variant variant_info(int v) {
+  switch (v) {
+    case 1: return {256, 4};
+    case 2: return {128, 2};
+    default: return {256, 2};
+  }
+}
+
+// Launchers (rad_kernels.cu). All enqueue on `s` and return the launch error.
+cudaError_t launch_prepass(const LaunchArgs& a, int total_blocks, cudaStream_t s);
+cudaError_t launch_accumulate(int variant, const LaunchArgs& a, int grid, cudaStream_t s);
+int accumulate_blocks_per_sm(int variant);
+size_t accumulate_smem_bytes(int variant);
+cudaError_t launch_readout(const float* state, int mixed, const double* state64, int n_omega,
+                           int n_bins, const double* omega, rad_ff ff, double* coh, double* inc,
+                           double* tot, cudaStream_t s);
+cudaError_t launch_fp64(const double* omega, const double* dirs, int n_omega, int n_dir,
+                        long long n, const double* r, const double* beta, const double* bdot,
+                        const double* w, double t, double dt, double* state64, int* status,
+                        cudaStream_t s);
+cudaError_t launch_state_add(float* state, const float* other, int n_bins, cudaStream_t s);
+cudaError_t launch_state64_add(double* state, const double* other, int n_bins, cudaStream_t s);
+
+void count_launches(int n);
+
+}  // namespace radimpl

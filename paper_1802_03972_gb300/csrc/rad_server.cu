@@ -1,0 +1,460 @@
+// Continuous-batching request loop for radiation-diagnostic jobs.
+//
+// Jobs arrive at any time.  A scheduler thread admits waiting jobs in arrival
+// order while a slot is free and their device footprint fits the budget,
+// keeps each admitted job's amplitudes resident on the device, and in every
+// round takes the oldest pending step of every admitted job and runs them all
+// in one batched persistent launch (the same engine as rad_batch), so a job
+// that arrives while others run joins the next round.  Steps are copied into
+// per-job device staging slots on a separate copy stream (overlapping the
+// compute stream); a round waits only on the copies of the steps it uses.
+// After a finished job's last step its spectrum is read out and its device
+// memory is released for the next job.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "rad_batch_impl.h"
+#include "rad_ctx.h"
+
+using namespace radimpl;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double seconds_since(Clock::time_point t0) {
+  return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+bool device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct Slot {
+  double* d = nullptr;       // [10 * max_particles]: r, beta, beta_dot, w
+  cudaEvent_t ready = nullptr;
+  bool busy = false;         // holds a queued step
+};
+
+struct QueuedStep {
+  int slot = -1;                 // device slot, or -1 while held on the host
+  std::vector<double> host;      // host copy while the job waits for admission
+  long long n = 0;
+  double t = 0, dt = 0;
+};
+
+enum class JobState { Waiting, Active, Done, Failed };
+
+struct Job {
+  rad_job_id id = 0;
+  std::vector<double> omega, dirs;
+  rad_ff ff{};
+  long long max_particles = 0;
+  int max_queued = 1;
+  size_t footprint = 0;
+  JobState state = JobState::Waiting;
+  rad_ctx* ctx = nullptr;
+  std::vector<Slot> slots;
+  std::deque<QueuedStep> queue;
+  bool finished = false;
+  bool in_round = false;
+  rad_status err = RAD_OK;
+  std::vector<double> coh, inc, tot;
+  Clock::time_point t_submit, t_ready;
+};
+
+size_t estimate_footprint(const rad_job_desc& d) {
+  const size_t nb = (size_t)d.n_omega * d.n_dir;
+  const size_t chunks = 64;  // upper bound of the automatic chunk count used here
+  return nb * (64 + 24 + 32 * chunks) + (size_t)d.max_particles * 80 * (1 + d.max_queued) +
+         (size_t)d.n_omega * 48 + (size_t)d.n_dir * 72 + (1 << 16);
+}
+
+}  // namespace
+
+struct rad_server {
+  size_t budget = 0;
+  int max_slots = 1;
+  cudaStream_t compute = nullptr;
+  cudaStream_t copy = nullptr;
+  bool own_compute = false;
+  BatchCore core;
+  std::mutex mu;
+  std::condition_variable cv_sched, cv_done;
+  std::thread worker;
+  bool stop = false;
+  rad_job_id next_id = 1;
+  std::map<rad_job_id, std::unique_ptr<Job>> jobs;
+  std::deque<rad_job_id> waiting;
+  size_t footprint = 0, peak_footprint = 0;
+  rad_server_stats st{};
+  rad_status fatal = RAD_OK;
+
+  void loop();
+  rad_status admit_locked(Job& j);
+  void release_job_locked(Job& j);
+};
+
+rad_status rad_server::admit_locked(Job& j) {
+  rad_ctx* c = nullptr;
+  rad_status s = rad_create(j.omega.data(), (int32_t)j.omega.size(), j.dirs.data(),
+                            (int32_t)(j.dirs.size() / 3), j.ff, RAD_PREC_MIXED, compute, &c);
+  if (s != RAD_OK) return s;
+  j.ctx = c;
+  j.slots.resize(j.max_queued);
+  for (auto& sl : j.slots) {
+    if (cudaMalloc(&sl.d, sizeof(double) * 10 * (size_t)j.max_particles) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.ready, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return RAD_ENOMEM;
+    }
+  }
+  // Steps fed while waiting move from host memory to device slots.
+  int k = 0;
+  for (auto& q : j.queue) {
+    Slot& sl = j.slots[k];
+    if (cudaMemcpyAsync(sl.d, q.host.data(), sizeof(double) * q.host.size(),
+                        cudaMemcpyHostToDevice, copy) != cudaSuccess ||
+        cudaEventRecord(sl.ready, copy) != cudaSuccess)
+      return RAD_ECUDA;
+    sl.busy = true;
+    q.slot = k++;
+  }
+  if (cudaStreamSynchronize(copy) != cudaSuccess) return RAD_ECUDA;
+  for (auto& q : j.queue) {
+    q.host.clear();
+    q.host.shrink_to_fit();
+  }
+  j.state = JobState::Active;
+  return RAD_OK;
+}
+
+void rad_server::release_job_locked(Job& j) {
+  for (auto& sl : j.slots) {
+    if (sl.d) cudaFree(sl.d);
+    if (sl.ready) cudaEventDestroy(sl.ready);
+    sl.d = nullptr;
+    sl.ready = nullptr;
+  }
+  j.slots.clear();
+  if (j.ctx) rad_destroy(j.ctx);
+  j.ctx = nullptr;
+  footprint -= std::min(footprint, j.footprint);
+  st.active = std::max(0, st.active - 1);
+}
+
+void rad_server::loop() {
+  std::unique_lock<std::mutex> lk(mu);
+  while (!stop) {
+    // 1. admission, in arrival order, while slots and memory allow
+    while (!waiting.empty()) {
+      Job& j = *jobs[waiting.front()];
+      if (st.active >= max_slots || footprint + j.footprint > budget) break;
+      waiting.pop_front();
+      footprint += j.footprint;
+      peak_footprint = std::max(peak_footprint, footprint);
+      st.active++;
+      st.waiting = (int32_t)waiting.size();
+      st.admitted++;
+      const rad_status s = admit_locked(j);
+      if (s != RAD_OK) {
+        j.err = s;
+        j.state = JobState::Failed;
+        release_job_locked(j);
+        cv_done.notify_all();
+      }
+    }
+    // 2. one round: the oldest ready step of every active job
+    std::vector<rad_ctx*> ctxs;
+    std::vector<rad_step> steps;
+    std::vector<Job*> in_round;
+    for (auto& kv : jobs) {
+      Job& j = *kv.second;
+      if (j.state != JobState::Active || j.queue.empty()) continue;
+      QueuedStep& q = j.queue.front();
+      if (q.slot < 0) continue;
+      Slot& sl = j.slots[q.slot];
+      const long long n = q.n;
+      rad_step s;
+      s.n = n;
+      s.r = sl.d;
+      s.beta = sl.d + 3 * n;
+      s.beta_dot = sl.d + 6 * n;
+      s.w = sl.d + 9 * n;
+      s.t = q.t;
+      s.dt = q.dt;
+      cudaStreamWaitEvent(compute, sl.ready, 0);
+      ctxs.push_back(j.ctx);
+      steps.push_back(s);
+      in_round.push_back(&j);
+      j.in_round = true;
+    }
+    // 3. finished jobs with nothing queued: read out and release
+    std::vector<Job*> to_read;
+    for (auto& kv : jobs) {
+      Job& j = *kv.second;
+      if (j.state == JobState::Active && j.finished && j.queue.empty() && !j.in_round)
+        to_read.push_back(&j);
+    }
+    if (ctxs.empty() && to_read.empty()) {
+      cv_sched.wait_for(lk, std::chrono::milliseconds(20));
+      continue;
+    }
+    lk.unlock();
+    rad_status rs = RAD_OK;
+    if (!ctxs.empty()) {
+      rs = core.run(ctxs.data(), steps.data(), (int)ctxs.size(), false);
+      if (rs == RAD_OK && cudaStreamSynchronize(compute) != cudaSuccess) rs = RAD_ECUDA;
+    }
+    for (Job* j : to_read) {
+      const size_t nb = (size_t)j->ctx->n_bins;
+      j->coh.resize(nb);
+      j->inc.resize(nb);
+      j->tot.resize(nb);
+      j->err = rad_spectrum(j->ctx, j->coh.data(), j->inc.data(), j->tot.data());
+    }
+    lk.lock();
+    if (!ctxs.empty()) {
+      st.rounds++;
+      for (size_t i = 0; i < in_round.size(); ++i) {
+        Job& j = *in_round[i];
+        j.in_round = false;
+        QueuedStep& q = j.queue.front();
+        j.slots[q.slot].busy = false;
+        j.queue.pop_front();
+        if (rs != RAD_OK) {
+          j.err = rs;
+          j.state = JobState::Failed;
+        } else {
+          st.updates += steps[i].n * (long long)j.ctx->n_bins;
+        }
+      }
+      if (rs == RAD_ECUDA) fatal = RAD_ECUDA;
+    }
+    for (Job* j : to_read) {
+      j->t_ready = Clock::now();
+      j->state = (j->err == RAD_OK || j->err == RAD_EDATA) ? JobState::Done : JobState::Failed;
+      st.completed++;
+      release_job_locked(*j);
+    }
+    cv_done.notify_all();
+    cv_sched.notify_all();  // feeders waiting on full queues
+  }
+}
+
+extern "C" {
+
+rad_status rad_server_create(size_t hbm_budget, int32_t max_slots, void* stream, rad_server** out) {
+  if (!out) return RAD_EINVAL;
+  *out = nullptr;
+  if (hbm_budget == 0 || max_slots < 1) return RAD_EINVAL;
+  rad_server* s = new (std::nothrow) rad_server();
+  if (!s) return RAD_ENOMEM;
+  s->budget = hbm_budget;
+  s->max_slots = max_slots;
+  s->compute = (cudaStream_t)stream;
+  if (!s->compute) {
+    if (cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      return RAD_ECUDA;
+    }
+    s->own_compute = true;
+  }
+  if (cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess) {
+    if (s->own_compute) cudaStreamDestroy(s->compute);
+    delete s;
+    return RAD_ECUDA;
+  }
+  rad_status st = s->core.init(max_slots, s->compute);
+  if (st != RAD_OK) {
+    s->core.release();
+    cudaStreamDestroy(s->copy);
+    if (s->own_compute) cudaStreamDestroy(s->compute);
+    delete s;
+    return st;
+  }
+  s->worker = std::thread([s] { s->loop(); });
+  *out = s;
+  return RAD_OK;
+}
+
+rad_status rad_job_submit(rad_server* s, const rad_job_desc* d, rad_job_id* id) {
+  if (!s || !d || !id || !d->omega || !d->dirs) return RAD_EINVAL;
+  if (d->n_omega < 1 || d->n_dir < 1 || d->max_particles < 1 || d->max_queued < 1)
+    return RAD_EINVAL;
+  if ((long long)d->n_omega * d->n_dir > 0x7fffffffLL) return RAD_EINVAL;
+  auto j = std::make_unique<Job>();
+  j->omega.assign(d->omega, d->omega + d->n_omega);
+  j->dirs.assign(d->dirs, d->dirs + 3 * (size_t)d->n_dir);
+  j->ff = d->ff;
+  j->max_particles = d->max_particles;
+  j->max_queued = d->max_queued;
+  j->footprint = estimate_footprint(*d);
+  if (j->footprint > s->budget) return RAD_EINVAL;
+  j->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->fatal != RAD_OK) return RAD_ESTATE;
+  j->id = s->next_id++;
+  *id = j->id;
+  s->waiting.push_back(j->id);
+  s->st.submitted++;
+  s->st.waiting = (int32_t)s->waiting.size();
+  s->jobs[j->id] = std::move(j);
+  s->cv_sched.notify_all();
+  return RAD_OK;
+}
+
+rad_status rad_job_feed(rad_server* s, rad_job_id id, const rad_step* step) {
+  if (!s || !step) return RAD_EINVAL;
+  if (step->n < 0 || !isfinite(step->t) || !isfinite(step->dt) || !(step->dt > 0.0))
+    return RAD_EINVAL;
+  if (step->n > 0 && (!step->r || !step->beta || !step->beta_dot || !step->w)) return RAD_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return RAD_EINVAL;
+  Job& j = *it->second;
+  if (j.finished || j.state == JobState::Done) return RAD_ESTATE;
+  if (j.state == JobState::Failed) return j.err == RAD_OK ? RAD_ESTATE : j.err;
+  if (step->n == 0) return RAD_OK;
+  if (step->n > j.max_particles) return RAD_EINVAL;
+  if ((int)j.queue.size() >= j.max_queued) return RAD_EBUSY;
+  const long long n = step->n;
+  const double* src[4] = {step->r, step->beta, step->beta_dot, step->w};
+  const size_t cnt[4] = {(size_t)3 * n, (size_t)3 * n, (size_t)3 * n, (size_t)n};
+  QueuedStep q;
+  q.n = n;
+  q.t = step->t;
+  q.dt = step->dt;
+  if (j.state == JobState::Waiting) {
+    q.host.resize((size_t)10 * n);
+    size_t off = 0;
+    for (int i = 0; i < 4; ++i) {
+      if (cudaMemcpy(q.host.data() + off, src[i], cnt[i] * sizeof(double), cudaMemcpyDefault) !=
+          cudaSuccess)
+        return RAD_ECUDA;
+      off += cnt[i];
+    }
+  } else {
+    int k = 0;
+    while (k < (int)j.slots.size() && j.slots[k].busy) ++k;
+    if (k == (int)j.slots.size()) return RAD_EBUSY;
+    Slot& sl = j.slots[k];
+    size_t off = 0;
+    for (int i = 0; i < 4; ++i) {
+      if (cudaMemcpyAsync(sl.d + off, src[i], cnt[i] * sizeof(double), cudaMemcpyDefault,
+                          s->copy) != cudaSuccess)
+        return RAD_ECUDA;
+      off += cnt[i];
+    }
+    if (cudaEventRecord(sl.ready, s->copy) != cudaSuccess) return RAD_ECUDA;
+    // The caller may reuse its buffers on return.
+    const bool host_src = !(device_ptr(step->r) && device_ptr(step->beta) &&
+                            device_ptr(step->beta_dot) && device_ptr(step->w));
+    if (host_src && cudaEventSynchronize(sl.ready) != cudaSuccess) return RAD_ECUDA;
+    if (!host_src && cudaEventSynchronize(sl.ready) != cudaSuccess) return RAD_ECUDA;
+    sl.busy = true;
+    q.slot = k;
+  }
+  j.queue.push_back(std::move(q));
+  s->cv_sched.notify_all();
+  return RAD_OK;
+}
+
+rad_status rad_job_finish(rad_server* s, rad_job_id id) {
+  if (!s) return RAD_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return RAD_EINVAL;
+  it->second->finished = true;
+  s->cv_sched.notify_all();
+  return RAD_OK;
+}
+
+rad_status rad_job_poll(rad_server* s, rad_job_id id, int32_t* done) {
+  if (!s || !done) return RAD_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return RAD_EINVAL;
+  const JobState js = it->second->state;
+  *done = (js == JobState::Done || js == JobState::Failed) ? 1 : 0;
+  return RAD_OK;
+}
+
+rad_status rad_job_result(rad_server* s, rad_job_id id, double timeout_s, double* coh,
+                          double* inc, double* tot, double* latency_s) {
+  if (!s) return RAD_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return RAD_EINVAL;
+  Job& j = *it->second;
+  auto ready = [&] { return j.state == JobState::Done || j.state == JobState::Failed; };
+  if (timeout_s < 0) {
+    s->cv_done.wait(lk, ready);
+  } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) {
+    return RAD_ETIMEOUT;
+  }
+  rad_status r = j.state == JobState::Done ? j.err : (j.err == RAD_OK ? RAD_ESTATE : j.err);
+  if (j.state == JobState::Done) {
+    const size_t nb = j.coh.size();
+    if (coh) memcpy(coh, j.coh.data(), nb * sizeof(double));
+    if (inc) memcpy(inc, j.inc.data(), nb * sizeof(double));
+    if (tot) memcpy(tot, j.tot.data(), nb * sizeof(double));
+  }
+  if (latency_s)
+    *latency_s = std::chrono::duration<double>(j.t_ready - j.t_submit).count();
+  s->jobs.erase(it);
+  return r;
+}
+
+rad_status rad_server_stats_get(rad_server* s, rad_server_stats* out) {
+  if (!s || !out) return RAD_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->st;
+  out->footprint_bytes = (int64_t)s->footprint;
+  out->peak_footprint_bytes = (int64_t)s->peak_footprint;
+  out->waiting = (int32_t)s->waiting.size();
+  return RAD_OK;
+}
+
+void rad_server_destroy(rad_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv_sched.notify_all();
+  }
+  if (s->worker.joinable()) s->worker.join();
+  cudaStreamSynchronize(s->compute);
+  cudaStreamSynchronize(s->copy);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto& kv : s->jobs) {
+      Job& j = *kv.second;
+      if (j.state == JobState::Active) s->release_job_locked(j);
+    }
+    s->jobs.clear();
+  }
+  s->core.release();
+  cudaStreamDestroy(s->copy);
+  if (s->own_compute) cudaStreamDestroy(s->compute);
+  delete s;
+}
+
+}  // extern "C"

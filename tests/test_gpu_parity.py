@@ -1,0 +1,186 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: relative spectral error per direction (2-norm over frequencies)
+<= 1e-5 for the mixed-precision path on the total spectrum and on its
+coherent and incoherent parts; <= 1e-9 for the plain FP64 kernel.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import TOL_FP64, TOL_TOTAL, gpu_run, oracle_run, row_error, spectra_grid, to_dev
+from paper_1802_03972_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1802_03972_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_1802_03972_gb300 import rad  # noqa: E402
+
+
+def check(ctx, ref, tol=TOL_TOTAL, parts=("tot", "coh", "inc"), ff=None):
+    coh, inc, tot = ctx.spectrum(ff=ff)
+    got = {"coh": coh, "inc": inc, "tot": tot}
+    errs = {}
+    for k in parts:
+        errs[k] = row_error(got[k], ref[k])
+        assert errs[k] <= tol, (k, errs)
+    return errs
+
+
+@pytest.fixture(scope="module")
+def helix():
+    wl = inputs.tiny_helix()
+    return wl, spectra_grid(oracle_run(wl, range(wl.n_steps)), wl)
+
+
+def test_tiny_helix_mixed_and_fp64(helix):
+    """64 point particles on helices, 1000 steps, 128 x 16 bins (full grid)."""
+    wl, ref = helix
+    ctx = gpu_run(wl, range(wl.n_steps))
+    check(ctx, ref, parts=("tot", "coh"))
+    assert np.all(ctx.spectrum()[1] == 0.0)  # point shape: no incoherent part
+    ctx64 = gpu_run(wl, range(wl.n_steps), prec=rad.PREC_FP64)
+    check(ctx64, ref, tol=TOL_FP64, parts=("tot", "coh"))
+
+
+def test_tiny_helix_host_buffers_match_device(helix):
+    wl, _ = helix
+    a = gpu_run(wl, range(50))
+    b = gpu_run(wl, range(50), host=True)
+    for x, y in zip(a.spectrum(), b.spectrum()):
+        np.testing.assert_array_equal(x, y)
+
+
+def small_lwfa(n=2000, n_omega=100, n_side=8, seed=21):
+    wl = inputs.lwfa_bunch(n_particles=n, n_omega=n_omega, n_side=n_side, seed=seed)
+    return wl
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_lwfa_small_full_grid_all_variants(variant):
+    """LWFA-shaped bunch with weights, Gaussian form factor, ragged particle count
+    (2000 = 31 x 64 + 16) and ragged frequency tile (100 of 128), 20 steps."""
+    wl = small_lwfa()
+    ref = spectra_grid(oracle_run(wl, range(20)), wl)
+    ctx = gpu_run(wl, range(20), tile=(variant, 0, 0))
+    check(ctx, ref)
+
+
+def test_lwfa_readout_with_other_shapes():
+    """One accumulation read out with CIC, TSC, QSC and point shapes (the shape
+    enters at readout only)."""
+    wl = small_lwfa(n=700, n_omega=64, n_side=4)
+    acc = oracle_run(wl, range(10))
+    ctx = gpu_run(wl, range(10))
+    for kind, width in ((oracle.FF_CIC, 0.1e-6), (oracle.FF_TSC, 0.2e-6), (oracle.FF_QSC, 0.05e-6),
+                        (oracle.FF_POINT, 0.0)):
+        ref = spectra_grid(acc, wl, (kind, width))
+        check(ctx, ref, ff=(kind, width), parts=("tot", "coh") + (("inc",) if kind else ()))
+
+
+def test_lwfa_full_size_sampled_rows():
+    """Full LWFA size (1e5 macro-particles, 512 log omega, 16 x 16 directions) in the
+    benchmark's launch configuration, 4 steps; the oracle computes 3 sampled
+    directions over all 512 frequencies (the gated per-direction error)."""
+    wl = inputs.lwfa_bunch()
+    steps = range(0, 4)
+    ctx = gpu_run(wl, steps)
+    coh, inc, tot = ctx.spectrum()
+    rows = [0, 137, 255]
+    bins = [(d, o) for d in rows for o in range(512)]
+    ref = {k: v.reshape(len(rows), 512) for k, v in oracle_run(wl, steps, bins).spectra().items()}
+    for k, g in (("tot", tot), ("coh", coh), ("inc", inc)):
+        assert row_error(g[rows], ref[k]) <= TOL_TOTAL, k
+
+
+def test_edge_cases_small_sizes():
+    """n = 1, n_omega = 1, n_dir = 1, zero-particle calls."""
+    for n, no, nd in ((1, 1, 1), (1, 3, 2), (65, 1, 5), (3, 130, 1)):
+        wl = inputs.lwfa_bunch(n_particles=n, n_omega=no, n_side=1, seed=n + no)
+        wl.dirs = inputs.dirs_grid(0.01, nd, 1) if nd > 1 else np.array([[0.0, 0.0, 1.0]])
+        ref = spectra_grid(oracle_run(wl, range(5)), wl)
+        ctx = gpu_run(wl, range(5))
+        z = to_dev(np.zeros(0))
+        ctx.accumulate(to_dev(np.zeros((3, 0))), to_dev(np.zeros((3, 0))), to_dev(np.zeros((3, 0))),
+                       z, 1e-15, 1e-16)
+        check(ctx, ref)
+
+
+def test_invalid_particles_reported_and_skipped():
+    wl = small_lwfa(n=300, n_omega=64, n_side=2)
+    good = oracle_run(wl, range(3))
+    ref = spectra_grid(good, wl)
+    from paper_1802_03972_gb300 import rad as R
+    ctx = R.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
+    for s in range(3):
+        st = wl.step(s)
+        # append two bad particles: NaN position and |beta| > 1
+        r = np.concatenate([st.r.reshape(3, -1), np.array([[np.nan, 0.0], [0.0, 0.0], [0.0, 0.0]])], 1)
+        b = np.concatenate([st.beta.reshape(3, -1), np.array([[0.0, 0.0], [0.0, 0.0], [0.5, 1.5]])], 1)
+        bd = np.concatenate([st.beta_dot.reshape(3, -1), np.ones((3, 2)) * 1e13], 1)
+        w = np.concatenate([st.w, [10.0, 10.0]])
+        ctx.accumulate(to_dev(r), to_dev(b), to_dev(bd), to_dev(w), st.t, st.dt)
+    with pytest.raises(R.RadError) as ei:
+        ctx.spectrum()
+    assert ei.value.status == R.RAD_EDATA
+    check(ctx, ref)  # reported once; the bad particles contributed nothing
+
+
+def test_wide_bunch_uses_wide_phase_path():
+    """Particles spread over 2 mm at omega up to 1e20 rad/s: |omega dtau| exceeds the
+    fast path's 2^21 turns and the FP64 phase path must still match."""
+    rng = np.random.default_rng(9)
+    n = 200
+    omega = inputs.omega_log(1e18, 1e20, 64)
+    dirs = inputs.dirs_grid(0.01, 2, 2)
+    r = np.stack([rng.normal(0, 1e-6, n), rng.normal(0, 1e-6, n), rng.uniform(-1e-3, 1e-3, n)])
+    b = np.stack([rng.normal(0, 1e-3, n), rng.normal(0, 1e-3, n), np.zeros(n)])
+    b[2] = np.sqrt(1 - 1e-5 - b[0] ** 2 - b[1] ** 2)
+    bd = rng.normal(0, 1e13, (3, n))
+    w = rng.uniform(1, 10, n)
+    bo, bdir = oracle.grid_bins(omega, dirs)
+    acc = oracle.Accumulator(bo, bdir)
+    ctx = rad.Context(omega, dirs)
+    for s in range(3):
+        t = s * 1e-16
+        acc.accumulate(r, b, bd, w, t, 1e-16)
+        ctx.accumulate(to_dev(r), to_dev(b), to_dev(bd), to_dev(w), t, 1e-16)
+        r = r + b * 299792458.0 * 1e-16
+    ref = {k: v.reshape(4, 64) for k, v in acc.spectra().items()}
+    check(ctx, ref, parts=("tot",))
+
+
+def test_deterministic_bitwise():
+    wl = small_lwfa(n=3000, n_omega=128, n_side=4)
+    a = gpu_run(wl, range(4)).spectrum()
+    b = gpu_run(wl, range(4)).spectrum()
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_large_time_offset():
+    """A common time offset of 0.1 ns (omega t ~ 1e10 rad at 1e20 rad/s) only changes
+    a common phase per call: the per-call reference keeps the fast path exact."""
+    wl = small_lwfa(n=500, n_omega=64, n_side=2)
+    shifted = inputs.Workload(wl.name, wl.omega, wl.dirs, wl.bunch, wl.n_steps, wl.dt, wl.ff_kind,
+                              wl.ff_width)
+    T = 1e-10
+
+    def step(s, base=wl):
+        st = base.step(s)
+        st.t += T
+        st.r = st.r.copy()
+        st.r[2 * st.n:] += 299792458.0 * T  # bunch moved on by c T along z
+        return st
+    shifted.step = step
+    ref = spectra_grid(oracle_run(shifted, range(4)), shifted)
+    ctx = gpu_run(shifted, range(4))
+    check(ctx, ref, parts=("tot",))
