@@ -260,6 +260,50 @@ rad_status rad_profile_enable(rad_ctx* ctx, int32_t on);
 rad_status rad_profile_read(rad_ctx* ctx, double* prepass_ms, double* accumulate_ms,
                             int64_t* calls);
 
+/* Accumulation without any allocation.
+ *
+ * Some callers cannot allocate device memory: code running inside a host
+ * application that owns the GPU's memory pool, a plug-in called from a
+ * time-step loop that forbids cudaMalloc (it would synchronise the device and
+ * stall the simulation), or a process that must keep its footprint fixed.
+ * rad_accumulate_static serves them.  It adds one time step into accumulators
+ * the caller owns and calls no cudaMalloc, cudaFree or allocating library
+ * routine.  Its working memory (grid tables, per-particle records, per-chunk
+ * partial sums, counters) is one file-scope device array of
+ * RAD_STATIC_SCRATCH_BYTES (about 14 MB).  Every GPU that loads the library
+ * holds that array until the process exits.  It is not a counterpart of
+ * anything in the paper.
+ *
+ *  omega   device [n_omega] angular frequencies, rad/s (> 0).
+ *  dirs    device [n_dir][3] observation directions (normalised here).
+ *  n, r, beta, beta_dot, w, t, dt   as rad_accumulate; device arrays only.
+ *  state   device float [16][n_omega * n_dir], read and updated: the same
+ *          layout as a context's accumulators (U.e1, U.e2, V.e1, V.e2 re/im
+ *          compensated sums, then their compensations; the same bytes as the
+ *          payload of rad_state_export for a MIXED context with these grids).
+ *          Zero it to start a new accumulation.
+ *  stream  cudaStream_t (NULL = legacy default stream).
+ * Limits: n_omega <= RAD_STATIC_MAX_OMEGA, n_dir <= RAD_STATIC_MAX_DIRS,
+ * n_omega * n_dir <= RAD_STATIC_MAX_BINS, n <= RAD_STATIC_MAX_PARTICLES.
+ * Larger sizes return RAD_EINVAL before anything is enqueued.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call shares the one array and clears what must start at zero.
+ * Calls whose work overlaps on the GPU (other streams or threads) race on it,
+ * so serialise them.  Particles with invalid data contribute nothing, and no
+ * status word reports them.  Returns RAD_OK once the work is enqueued,
+ * RAD_EINVAL for bad arguments, or RAD_ECUDA if the set-up or a launch failed. */
+#define RAD_STATIC_MAX_OMEGA 4096
+#define RAD_STATIC_MAX_DIRS 4096
+#define RAD_STATIC_MAX_BINS 65536
+#define RAD_STATIC_MAX_PARTICLES 65536
+#define RAD_STATIC_SCRATCH_BYTES (14u << 20)
+rad_status rad_accumulate_static(const double* omega, int32_t n_omega, const double* dirs,
+                                 int32_t n_dir, int64_t n, const double* r, const double* beta,
+                                 const double* beta_dot, const double* w, double t, double dt,
+                                 float* state, void* stream);
+
 /* Diagnostics. */
 const char* rad_status_str(rad_status s);
 /* rad_last_error - last non-OK status of this context (sticky until reset). */

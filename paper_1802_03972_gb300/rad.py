@@ -30,8 +30,11 @@ EXPORTS = [
     "rad_batch_sync", "rad_batch_destroy", "rad_server_create", "rad_job_submit", "rad_job_feed",
     "rad_job_finish", "rad_job_poll", "rad_job_result", "rad_server_stats_get",
     "rad_server_destroy", "rad_status_str", "rad_last_error", "rad_kernel_launch_count",
-    "rad_probe_peaks", "rad_profile_enable", "rad_profile_read",
+    "rad_probe_peaks", "rad_profile_enable", "rad_profile_read", "rad_accumulate_static",
 ]
+
+# Limits of rad_accumulate_static (include/rad.h).
+STATIC_MAX_OMEGA, STATIC_MAX_DIRS, STATIC_MAX_BINS, STATIC_MAX_PARTICLES = 4096, 4096, 65536, 65536
 
 
 class RadError(RuntimeError):
@@ -115,6 +118,7 @@ def load(path: str = LIB_PATH):
         "rad_probe_peaks": (ctypes.c_int, [vp, ctypes.c_int]),
         "rad_profile_enable": (st, [vp, i32]),
         "rad_profile_read": (st, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(i64)]),
+        "rad_accumulate_static": (st, [vp, i32, vp, i32, i64, vp, vp, vp, vp, dbl, dbl, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -277,6 +281,22 @@ class Context:
         _check(self._lib.rad_profile_read(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
                "rad_profile_read")
         return a.value, b.value, n.value
+
+
+def accumulate_static(omega, dirs, r, beta, beta_dot, w, t: float, dt: float, state,
+                      stream=None) -> None:
+    """rad_accumulate_static: one step into caller-owned accumulators `state`
+    (device float32 [16][n_omega * n_dir]) with no allocation by the library.
+    omega [n_omega], dirs [n_dir][3] and the particle arrays are float64 device
+    tensors; see include/rad.h for the limits."""
+    n = int(w.shape[0])
+    _check_particles(n, r, beta, beta_dot, w)
+    n_omega = int(omega.shape[0])
+    n_dir = int(dirs.numel() // 3) if hasattr(dirs, "numel") else int(np.asarray(dirs).size // 3)
+    _check(load().rad_accumulate_static(_ptr(omega), n_omega, _ptr(dirs), n_dir, n, _ptr(r),
+                                        _ptr(beta), _ptr(beta_dot), _ptr(w), float(t), float(dt),
+                                        _ptr(state), _stream_handle(stream)),
+           "rad_accumulate_static")
 
 
 def make_step(n, r, beta, beta_dot, w, t, dt) -> rad_step:
