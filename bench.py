@@ -49,6 +49,14 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep the default tile instead of rad_tune")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-rounds", type=int, default=3)
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-jobs", type=int, default=24)
+    p.add_argument("--serve-load", type=float, default=0.7,
+                   help="arrival rate as a fraction of measured capacity")
+    p.add_argument("--serve-rate", type=float, default=None,
+                   help="fixed arrival rate (jobs/s) instead of --serve-load")
     p.add_argument("--peaks", action="store_true", help="also run the pipe-throughput probe")
     return p.parse_args()
 
@@ -193,6 +201,113 @@ def reference_arm(args, wl):
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def batch_leg(rounds: int, n_jobs: int = 64):
+    """64 independent jobs (the batched job mix) advanced one step per round in one
+    persistent launch, CUDA-graph replayed; against the same jobs launched one
+    context at a time.  Returns a dict for the JSON line."""
+    import torch
+
+    from paper_1802_03972_gb300 import inputs, rad
+    specs = inputs.job_mix(n_jobs)
+    wls = [s.workload() for s in specs]
+    dev, ctxs = [], []
+    for wl in wls:
+        st = wl.step(0)
+        dev.append([torch.from_numpy(a).cuda() for a in (st.r, st.beta, st.beta_dot, st.w)])
+        ctxs.append(rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width))
+    upd = sum(s.updates_per_step() for s in specs)
+    batch = rad.Batch(ctxs)
+
+    def steps(r):
+        return [rad.make_step(wl.n_particles, *d, r * wl.dt, wl.dt) for wl, d in zip(wls, dev)]
+
+    batch.accumulate(steps(0))  # captures the graph
+    batch.sync()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for r in range(1, rounds + 1):
+        batch.accumulate(steps(r))
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3 / rounds
+    # unbatched: one launch pair per job per round, in submission order
+    e0.record()
+    for c, wl, d in zip(ctxs, wls, dev):
+        c.accumulate(*d, wl.dt, wl.dt)
+    e1.record()
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return {"jobs": n_jobs, "updates_per_round": upd, "rounds": rounds,
+            "value": upd / t_batch, "unit": UNIT, "ms_per_round": 1e3 * t_batch,
+            "unbatched_value": upd / t_seq, "batched_over_unbatched": t_seq / t_batch,
+            "graph_replay": True}
+
+
+def serve_leg(n_jobs: int, load: float, rate: float | None, steps_range=(5, 20), seed: int = 5):
+    """Continuous batching: Poisson arrivals of the batched job mix (steps per job
+    scaled to steps_range), each job fed step by step from device buffers; p50/p99
+    of arrival-to-result latency and the throughput of the window."""
+    import numpy as np
+    import torch
+
+    from paper_1802_03972_gb300 import inputs, rad
+    specs = inputs.job_mix(n_jobs, base_seed=5000, steps=steps_range)
+    wls = [s.workload() for s in specs]
+    work = [s.updates_per_step() * s.n_steps for s in specs]
+    dev = []
+    for wl in wls:
+        st = wl.step(0)
+        dev.append([torch.from_numpy(a).cuda() for a in (st.r, st.beta, st.beta_dot, st.w)])
+    cap = 1.6e12  # updates/s of one GB300 on this kernel (bench headline)
+    lam = rate if rate else load * cap / float(np.mean(work))
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, n_jobs))
+    srv = rad.Server(hbm_budget=150 << 30, max_slots=64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ids, fed, done, lat = [None] * n_jobs, [0] * n_jobs, [False] * n_jobs, [None] * n_jobs
+    nxt = 0
+    while not all(done):
+        now = time.perf_counter() - t0
+        busy = False
+        while nxt < n_jobs and arrivals[nxt] <= now:
+            wl = wls[nxt]
+            ids[nxt] = srv.submit(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width,
+                                  max_particles=wl.n_particles, max_queued=2)
+            nxt += 1
+            busy = True
+        for j in range(nxt):
+            if done[j]:
+                continue
+            wl = wls[j]
+            if fed[j] < specs[j].n_steps:
+                st = rad.make_step(wl.n_particles, *dev[j], fed[j] * wl.dt, wl.dt)
+                if srv.feed(ids[j], st) == rad.RAD_OK:
+                    fed[j] += 1
+                    busy = True
+                    if fed[j] == specs[j].n_steps:
+                        srv.finish(ids[j])
+            elif srv.poll(ids[j]):
+                *_, lat[j] = srv.result(ids[j], wl.dirs.shape[0], wl.omega.shape[0])
+                done[j] = True
+                busy = True
+        if not busy:
+            time.sleep(0.0005)
+    makespan = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"jobs": n_jobs, "arrival_rate_per_s": lam, "load": load if not rate else None,
+            "steps_per_job": list(steps_range), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+            "value": float(sum(work)) / makespan, "unit": UNIT, "makespan_s": makespan,
+            "rounds": stats["rounds"], "peak_footprint_bytes": stats["peak_footprint_bytes"]}
 
 
 def main():
@@ -356,6 +471,13 @@ def main():
         rate, cores, desc, _ = cpu_oracle_rate(wl, 64, 10.0)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
+    batched = None
+    if not args.no_batch and rank == 0:
+        batched = batch_leg(args.batch_rounds)
+    served = None
+    if not args.no_serve and rank == 0:
+        served = serve_leg(args.serve_jobs, args.serve_load, args.serve_rate)
+
     peaks = None
     if args.peaks and rank == 0:
         p = rad.probe_peaks()
@@ -368,7 +490,10 @@ def main():
                "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(wl),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clocks, "rel_err_sampled": rel_err, "fp64_plain": fp64}
+               "clocks": clocks, "rel_err_sampled": rel_err, "fp64_plain": fp64,
+               "batched": batched, "serving": served,
+               "p50_s": served["p50_s"] if served else None,
+               "p99_s": served["p99_s"] if served else None}
         if peaks:
             out["peaks"] = peaks
         print(json.dumps(out), flush=True)
