@@ -35,7 +35,13 @@ SM_MAX_MHZ = 2070.0
 MUFU_PER_CLK_SM = 16.0   # sin/cos lane-ops per clock per SM (measured by rad_probe_peaks)
 MUFU_PER_UPDATE = 2.0    # one sin and one cos per (particle, omega, n)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "accumulate_lwfa_traffic.json")
-KERNEL_SRC = os.path.join(ROOT, "paper_1802_03972_gb300", "csrc", "rad_kernels.cu")
+VARIANT_NAMES = {0: "FP32 FMA, 256 threads x 2 omega, 3 CTAs/SM",
+                 1: "FP32 FMA, 256 threads x 4 omega, 2 CTAs/SM",
+                 2: "FP32 FMA, 128 threads x 2 omega, 6 CTAs/SM",
+                 3: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads, 3 CTAs/SM",
+                 4: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads, 4 CTAs/SM",
+                 5: "FP32 FMA, 256 threads x 2 omega, 4 CTAs/SM"}
+KERNEL_SRC = os.path.join(ROOT, "paper_1802_03972_gb300", "csrc", "rad_accumulate.cu")
 
 
 def parse():
@@ -49,6 +55,7 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep the default tile instead of rad_tune")
+    p.add_argument("--tile", default=None, help="fixed tile 'variant,omega_tile,chunk' (no tuning)")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-rounds", type=int, default=3)
     p.add_argument("--no-serve", action="store_true")
@@ -122,14 +129,14 @@ def kernel_hash() -> str:
     return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
 
 
-def traffic_per_launch(updates_per_step: int):
+def traffic_per_launch(updates_per_step: int, tile):
     """DRAM bytes per accumulate launch from the committed ncu summary, scaled to this
-    launch's updates; None when the kernel source changed since the capture."""
+    launch's updates; None when the kernel source or the tile changed since the capture."""
     try:
         t = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
         return None
-    if t.get("kernel_sha") != kernel_hash():
+    if t.get("kernel_sha") != kernel_hash() or list(t.get("tile", [])) != list(tile):
         return None
     return t["dram_bytes_per_launch"] * updates_per_step / t["updates_per_launch"]
 
@@ -343,7 +350,11 @@ def main():
                 for st in steps_host]
     upd = wl.updates_per_step()
     ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
-    tile = ctx.tune(wl.n_particles) if not args.no_tune else ctx.get_tile()
+    if args.tile:
+        ctx.set_tile(*[int(x) for x in args.tile.split(",")])
+        tile = ctx.get_tile()
+    else:
+        tile = ctx.tune(wl.n_particles) if not args.no_tune else ctx.get_tile()
 
     def run(k):
         st = steps_host[k % ring]
@@ -406,9 +417,9 @@ def main():
     achieved = upd / acc_s if acc_s > 0 else None
     peak = sm * MUFU_PER_CLK_SM * SM_MAX_MHZ * 1e6 / MUFU_PER_UPDATE
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
-            "frac": achieved / peak if achieved else None, "traffic": traffic_per_launch(upd),
+            "frac": achieved / peak if achieved else None, "traffic": traffic_per_launch(upd, tile),
             "kernel": "accumulate_kernel variant %d (%s), omega tile %d, chunk %s" % (
-                tile[0], {0: "256 threads x 2 omega", 1: "256 x 4", 2: "128 x 2"}[tile[0]], tile[1],
+                tile[0], VARIANT_NAMES.get(tile[0], "?"), tile[1],
                 tile[2] or "auto"),
             "peak_basis": f"{sm} SMs x {MUFU_PER_CLK_SM:g} MUFU sin/cos per clk x {SM_MAX_MHZ:g} MHz "
                           f"(max SM clock) / {MUFU_PER_UPDATE:g} per update",
@@ -474,9 +485,11 @@ def main():
     batched = None
     if not args.no_batch and rank == 0:
         batched = batch_leg(args.batch_rounds)
-    served = None
+    served = served_literal = None
     if not args.no_serve and rank == 0:
         served = serve_leg(args.serve_jobs, args.serve_load, args.serve_rate)
+        # the literal arrival rate of the serving workload: 200 jobs/s, a window of 32
+        served_literal = serve_leg(32, args.serve_load, 200.0, seed=6)
 
     peaks = None
     if args.peaks and rank == 0:
@@ -491,7 +504,7 @@ def main():
                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(wl),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clocks, "rel_err_sampled": rel_err, "fp64_plain": fp64,
-               "batched": batched, "serving": served,
+               "batched": batched, "serving": served, "serving_literal_rate": served_literal,
                "p50_s": served["p50_s"] if served else None,
                "p99_s": served["p99_s"] if served else None}
         if peaks:

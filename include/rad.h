@@ -73,10 +73,16 @@ typedef enum {
 
 /* Form-factor choice. width is Delta (CIC/TSC/QSC) or sigma (GAUSS) in metres,
  * ignored for POINT.  The shape enters only at readout, so one accumulation can
- * be read out with several shapes (rad_spectrum_ff). */
+ * be read out with several shapes (rad_spectrum_ff).
+ * flags = RAD_FF_3D takes the box shapes as axis-aligned 3-D products
+ * rho(x) rho(y) rho(z) of the 1-D shape (Sec. 3.1-3.2), so the form factor
+ * depends on the direction: f(n, omega) = prod_d f_1(omega n_d).  Without it f
+ * depends on omega only (Table 1 with n along one axis, as printed).  The
+ * Gaussian is isotropic and ignores the flag. */
+#define RAD_FF_3D 1
 typedef struct {
-  int32_t kind;     /* rad_ff_kind */
-  int32_t reserved; /* must be 0 */
+  int32_t kind;  /* rad_ff_kind */
+  int32_t flags; /* 0 or RAD_FF_3D */
   double width;
 } rad_ff;
 

@@ -25,6 +25,7 @@ _SRC = os.path.join(_HERE, "rad_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 FF_POINT, FF_CIC, FF_TSC, FF_QSC, FF_GAUSS = 0, 1, 2, 3, 4
+FF_3D = 1  # ff_flags bit: box shapes as axis-aligned 3-D products (direction-dependent f)
 PER_BIN = 18  # U, V, P: complex 3-vectors
 
 _lib = None
@@ -52,12 +53,17 @@ def _load():
     lib.oracle_k0.restype = ctypes.c_double
     lib.oracle_form_factor.restype = ctypes.c_double
     lib.oracle_form_factor.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lib.oracle_form_factor_dir.restype = ctypes.c_double
+    lib.oracle_form_factor_dir.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, dp]
     lib.oracle_amplitude.argtypes = [dp, dp, dp, dp]
     lib.oracle_accumulate.argtypes = [i64, dp, dp, i64, dp, dp, dp, dp, ctypes.c_double,
-                                      ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp]
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, dp, dp]
     lib.oracle_accumulate_particles.argtypes = [i64, dp, dp, i64, dp, dp, dp, ctypes.c_double,
                                                 ctypes.c_double, dp]
-    lib.oracle_readout.argtypes = [i64, dp, dp, dp, ctypes.c_int, ctypes.c_double, dp, dp, dp, dp]
+    lib.oracle_readout.argtypes = [i64, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_double, dp, dp, dp, dp]
     lib.oracle_num_threads.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -85,6 +91,12 @@ def form_factor(kind: int, width: float, omega) -> np.ndarray:
     lib = _load()
     om = np.atleast_1d(_f64(omega))
     return np.array([lib.oracle_form_factor(int(kind), float(width), float(w)) for w in om])
+
+
+def form_factor_dir(kind: int, flags: int, width: float, omega: float, n) -> float:
+    """f(n, omega): Table 1, or with FF_3D the axis-aligned 3-D product of the box shape."""
+    n = _f64(n)
+    return _load().oracle_form_factor_dir(int(kind), int(flags), float(width), float(omega), _p(n))
 
 
 def amplitude(n, beta, bdot) -> np.ndarray:
@@ -116,11 +128,12 @@ def grid_bins(omega, dirs, bins=None):
 class Accumulator:
     """Running oracle sums over a set of bins (Eq. 13, split and literal)."""
 
-    def __init__(self, bin_omega, bin_dir, ff_kind: int = FF_POINT, ff_width: float = 0.0):
+    def __init__(self, bin_omega, bin_dir, ff_kind: int = FF_POINT, ff_width: float = 0.0,
+                 ff_flags: int = 0):
         self.bin_omega = _f64(bin_omega).ravel()
         self.bin_dir = _f64(bin_dir).reshape(-1, 3)
         assert self.bin_dir.shape[0] == self.bin_omega.shape[0]
-        self.ff_kind, self.ff_width = int(ff_kind), float(ff_width)
+        self.ff_kind, self.ff_width, self.ff_flags = int(ff_kind), float(ff_width), int(ff_flags)
         nb = self.bin_omega.shape[0]
         self.acc = np.zeros((nb, PER_BIN))
         self.comp = np.zeros((nb, PER_BIN))
@@ -136,7 +149,7 @@ class Accumulator:
         assert r.size == 3 * N and beta.size == 3 * N and bd.size == 3 * N
         _load().oracle_accumulate(self.n_bins, _p(self.bin_omega), _p(self.bin_dir), N, _p(r),
                                   _p(beta), _p(bd), _p(w), float(t), float(dt), self.ff_kind,
-                                  self.ff_width, _p(self.acc), _p(self.comp))
+                                  self.ff_flags, self.ff_width, _p(self.acc), _p(self.comp))
 
     def amplitudes(self) -> dict:
         """Compensated complex sums: U, V, P as [n_bins][3] complex arrays."""
@@ -144,14 +157,17 @@ class Accumulator:
         z = s[:, 0::2] + 1j * s[:, 1::2]  # [nb][9]: U xyz, V xyz, P xyz
         return {"U": z[:, 0:3], "V": z[:, 3:6], "P": z[:, 6:9]}
 
-    def spectra(self, ff_kind: int | None = None, ff_width: float | None = None) -> dict:
+    def spectra(self, ff_kind: int | None = None, ff_width: float | None = None,
+                ff_flags: int | None = None) -> dict:
         """coh, inc, tot, paper spectra per bin for the given (or own) shape."""
         kind = self.ff_kind if ff_kind is None else int(ff_kind)
         width = self.ff_width if ff_width is None else float(ff_width)
+        flags = self.ff_flags if ff_flags is None else int(ff_flags)
         nb = self.n_bins
         out = {k: np.zeros(nb) for k in ("coh", "inc", "tot", "paper")}
-        _load().oracle_readout(nb, _p(self.bin_omega), _p(self.acc), _p(self.comp), kind, width,
-                               _p(out["coh"]), _p(out["inc"]), _p(out["tot"]), _p(out["paper"]))
+        _load().oracle_readout(nb, _p(self.bin_omega), _p(self.bin_dir), _p(self.acc),
+                               _p(self.comp), kind, flags, width, _p(out["coh"]), _p(out["inc"]),
+                               _p(out["tot"]), _p(out["paper"]))
         return out
 
 

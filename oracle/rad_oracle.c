@@ -41,7 +41,9 @@
  *    point-charge limit of Sec. 3.2 to give N^2);
  *  - sinc(x) = sin(x)/x, argument omega Delta / (2c) (Table 1);
  *  - the form factor depends on omega only (Table 1 as printed, which takes
- *    n along one axis without loss of generality, Sec. 3.2);
+ *    n along one axis without loss of generality, Sec. 3.2); with the 3-D flag
+ *    the box shapes are axis-aligned products rho(x) rho(y) rho(z) and f
+ *    depends on the direction too (oracle_form_factor_dir);
  *  - "incoherent" is weighted by w (1 - f^2), "coherent" by w^2 f^2: per
  *    macro-particle the same total as Eq. 12, N + (N^2 - N) f^2, with the
  *    inter-particle incoherence kept out of the incoherent part at low omega.
@@ -93,6 +95,23 @@ double oracle_form_factor(int kind, double width, double omega) {
   }
 }
 
+/* Bit of ff_flags: box shapes (CIC/TSC/QSC) taken as the 3-D product
+ * rho(x) rho(y) rho(z) of the 1-D shape along the coordinate axes (Sec. 3.1, 3.2:
+ * the charge distribution factorises per axis), so that for a direction n the
+ * phase factor of the offsets is the product over axes,
+ *   f(n, omega) = prod_d f_1(omega n_d),   f_1 as Table 1 with omega n_d.
+ * Without the bit (and always for the isotropic Gaussian) f depends on omega
+ * only: Table 1 as printed, n along one axis. */
+#define ORC_FF_3D 1
+
+double oracle_form_factor_dir(int kind, int flags, double width, double omega, const double n[3]) {
+  if (!(flags & ORC_FF_3D) || kind == ORC_FF_POINT || kind == ORC_FF_GAUSS)
+    return oracle_form_factor(kind, width, omega);
+  double f = 1.0;
+  for (int d = 0; d < 3; ++d) f *= oracle_form_factor(kind, width, omega * n[d]);
+  return f;
+}
+
 /* Neumaier's compensated summation: s + c carries the running sum. */
 static void nadd(double* s, double* c, double x) {
   const double t = *s + x;
@@ -125,21 +144,21 @@ void oracle_amplitude(const double n[3], const double beta[3], const double bdot
  * step dt to every bin b = (bin_omega[b], bin_dir[3b..3b+2]).
  *   r, beta, beta_dot: SoA [3][N] (x block, y block, z block), metres / 1 / 1/s
  *   w: [N] electrons per macro-particle (> 0)
- *   ff_kind, ff_width: the shape used for the paper's literal sum P
+ *   ff_kind, ff_flags, ff_width: the shape used for the paper's literal sum P
  *   acc, comp: [n_bins][18] running sums and their Neumaier compensation
  * Layout per bin: U (6 doubles), V (6), P (6), each (x,y,z) x (re,im).
  * Bins are independent and processed in parallel; within a bin the particle
  * order is fixed, so the result does not depend on the thread count. */
 void oracle_accumulate(int64_t n_bins, const double* bin_omega, const double* bin_dir,
                        int64_t N, const double* r, const double* beta, const double* beta_dot,
-                       const double* w, double t, double dt, int ff_kind, double ff_width,
-                       double* acc, double* comp) {
+                       const double* w, double t, double dt, int ff_kind, int ff_flags,
+                       double ff_width, double* acc, double* comp) {
   int64_t b;
 #pragma omp parallel for schedule(dynamic, 1)
   for (b = 0; b < n_bins; ++b) {
     const double omega = bin_omega[b];
     const double* n = bin_dir + 3 * b;
-    const double f = oracle_form_factor(ff_kind, ff_width, omega);
+    const double f = oracle_form_factor_dir(ff_kind, ff_flags, ff_width, omega, n);
     double* s = acc + ORC_PER_BIN * b;
     double* c = comp + ORC_PER_BIN * b;
     for (int64_t k = 0; k < N; ++k) {
@@ -192,14 +211,15 @@ void oracle_accumulate_particles(int64_t n_bins, const double* bin_omega, const 
 
 /* Readout of the spectra d^2I/dOmega domega for every bin (J s / sr per rad/s
  * in SI): coherent K0 f^2 |U|^2, incoherent K0 (1 - f^2) |V|^2, total their
- * sum, and the paper's literal K0 |P|^2. f is taken for (ff_kind, ff_width);
- * any output pointer may be NULL. */
-void oracle_readout(int64_t n_bins, const double* bin_omega, const double* acc, const double* comp,
-                    int ff_kind, double ff_width, double* coh, double* inc, double* tot,
-                    double* paper) {
+ * sum, and the paper's literal K0 |P|^2. f is taken for (ff_kind, ff_flags,
+ * ff_width) and the bin's direction; any output pointer may be NULL. */
+void oracle_readout(int64_t n_bins, const double* bin_omega, const double* bin_dir,
+                    const double* acc, const double* comp, int ff_kind, int ff_flags,
+                    double ff_width, double* coh, double* inc, double* tot, double* paper) {
   const double k0 = oracle_k0();
   for (int64_t b = 0; b < n_bins; ++b) {
-    const double f = oracle_form_factor(ff_kind, ff_width, bin_omega[b]);
+    const double f =
+        oracle_form_factor_dir(ff_kind, ff_flags, ff_width, bin_omega[b], bin_dir + 3 * b);
     double m2[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < 3; ++a)
       for (int j = 0; j < 6; ++j) {

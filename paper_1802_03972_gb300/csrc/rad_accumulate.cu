@@ -1,0 +1,676 @@
+// The accumulate kernel of the far-field radiation sum (Pausch et al. 2018,
+// Eq. 1 and the in-situ inner sum of Eq. 13).
+//
+// Persistent: one CTA per resident slot takes dynamic work items (job, bin
+// tile, particle chunk).  A bin tile is NT directions x WT frequencies; the
+// chunk's particle records (80 B each, written by the pre-pass) stream through
+// shared memory in tiles of THREADS / NT particles, fetched by a TMA bulk copy
+// (cp.async.bulk + mbarrier, time-bounded wait) one tile ahead of use.
+//
+// Stage 1, one (particle, direction) record per thread, FP32: the retarded-time
+// offset dtau = -n.(r - r_ref)/c as a float-float pair (TwoProduct with fma,
+// TwoSum), and the transverse amplitude components a_i = e_i . A in a basis
+// (e1, e2) perpendicular to n.  n . A = 0 (Eq. 1), so these two carry |A|^2;
+// with u = n - beta, n x (u x bdot) = u (n.bdot) - bdot D,
+// D = 1 - beta.n = (1/gamma^2 + b1^2 + b2^2) / (1 + beta.n) and e_i.u = -b_i,
+// a_i = -(b_i (n.bdot) + (e_i.bdot) D) / D^2, free of cancellation at high
+// gamma.  Records are double-buffered, one barrier per particle tile.
+//
+// Stage 2, per (particle, direction, frequency), the "amplitude update": the
+// phase in turns p = (omega/2pi) dtau is reduced exactly by one fused multiply-
+// add against 1.5 * 2^23 (no FRND, which shares the MUFU pipe), the float-float
+// cross terms are added in radians, and sin/cos come from the MUFU (2 per
+// update).  The weighted sums U_i += w dt a_i e^{i phi}, V_i += sqrt(w) dt a_i
+// e^{i phi} are then formed in one of two ways:
+//  * FP32 variants: 8 packed FMAs (f32x2) per update into register accumulators,
+//    two frequencies per packed lane pair;
+//  * tensor-core variants: per warp, a 16-frequency x 8-particle block of
+//    e^{i phi} is the A operand of mma.sync m16n8k8 TF32 and the 4 weighted
+//    amplitudes of the 8 particles are B.  Both are split into TF32 hi and lo
+//    parts (hi = the top 19 bits, lo = the exact rest), B's hi and lo side by
+//    side in the 8 N-columns, so two MMAs per cos/sin give all of
+//    hi.hi + hi.lo + lo.hi + lo.lo with FP32 accumulation.  This takes the
+//    accumulation FMAs off the FP32 pipe, which together with the phase
+//    arithmetic and MUFU issue is what limits the FP32 variants.
+// Sums are two-level (per particle tile, then per chunk).  Each work item
+// writes its partial sums; the last item of a bin tile to finish (an arrival
+// counter, no float atomics) adds the partials in chunk order, multiplies by
+// e^{i omega tau_ref(n)} (reduced in FP64) and adds the result into the
+// resident state with compensated (Kahan) FP32 sums.  Results are
+// deterministic for a given tile configuration.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rad_device.cuh"
+#include "rad_impl.h"
+
+namespace radimpl {
+
+namespace {
+
+using namespace dev;
+
+constexpr uint32_t kTf32Mask = 0xFFFFE000u;  // sign, exponent, 10 mantissa bits
+
+// Stage 1: record of (particle, direction).  raw: the particle's 80-byte record.
+// Returns false when |dtau| is beyond the fast phase path's range.
+__device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
+                                               const float* __restrict__ dt_, int n_dir, int d,
+                                               float tau_fast, float& th, float& tl, float amp[4]) {
+  const float4 q0 = *reinterpret_cast<const float4*>(raw);
+  const float4 q1 = *reinterpret_cast<const float4*>(raw + 4);
+  const float4 q2 = *reinterpret_cast<const float4*>(raw + 8);
+  const float4 q3 = *reinterpret_cast<const float4*>(raw + 12);
+  const float2 q4 = *reinterpret_cast<const float2*>(raw + 16);
+  const float sh0 = q0.x, sh1 = q0.y, sh2 = q0.z, sl0 = q0.w, sl1 = q1.x, sl2 = q1.y;
+  const float bh0 = q1.z, bh1 = q1.w, bh2 = q2.x, bl0 = q2.y, bl1 = q2.z, bl2 = q2.w;
+  const float ad0 = q3.x, ad1 = q3.y, ad2 = q3.z, g2 = q3.w, ww = q4.x, sw = q4.y;
+  const float nh0 = __ldg(dt_ + 0 * n_dir + d), nh1 = __ldg(dt_ + 1 * n_dir + d), nh2 = __ldg(dt_ + 2 * n_dir + d);
+  const float nl0 = __ldg(dt_ + 3 * n_dir + d), nl1 = __ldg(dt_ + 4 * n_dir + d), nl2 = __ldg(dt_ + 5 * n_dir + d);
+  const float e10 = __ldg(dt_ + 6 * n_dir + d), e11 = __ldg(dt_ + 7 * n_dir + d), e12 = __ldg(dt_ + 8 * n_dir + d);
+  const float e20 = __ldg(dt_ + 9 * n_dir + d), e21 = __ldg(dt_ + 10 * n_dir + d), e22 = __ldg(dt_ + 11 * n_dir + d);
+
+  // n . s in float-float: exact products (TwoProduct via fma) and exact sums
+  // (Knuth TwoSum) of the hi parts, all first-order lo terms added in FP32.
+  const float p0 = __fmul_rn(nh0, sh0), p1 = __fmul_rn(nh1, sh1), p2 = __fmul_rn(nh2, sh2);
+  float lo = __fadd_rn(__fadd_rn(fmaf(nh0, sh0, -p0), fmaf(nh1, sh1, -p1)), fmaf(nh2, sh2, -p2));
+  lo = fmaf(nh0, sl0, lo);
+  lo = fmaf(nh1, sl1, lo);
+  lo = fmaf(nh2, sl2, lo);
+  lo = fmaf(nl0, sh0, lo);
+  lo = fmaf(nl1, sh1, lo);
+  lo = fmaf(nl2, sh2, lo);
+  const float s1 = __fadd_rn(p0, p1);
+  float bb = __fsub_rn(s1, p0);
+  const float er1 = __fadd_rn(__fsub_rn(p0, __fsub_rn(s1, bb)), __fsub_rn(p1, bb));
+  const float s2 = __fadd_rn(s1, p2);
+  bb = __fsub_rn(s2, s1);
+  const float er2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, bb)), __fsub_rn(p2, bb));
+  lo = __fadd_rn(lo, __fadd_rn(er1, er2));
+  const float hi = __fadd_rn(s2, lo);
+  const float lo2 = __fsub_rn(lo, __fsub_rn(hi, s2));
+  th = -hi;
+  tl = -lo2;
+
+  // Transverse amplitude (see the file comment).
+  const float b1 = fmaf(e10, bh0, fmaf(e11, bh1, e12 * bh2)) + fmaf(e10, bl0, fmaf(e11, bl1, e12 * bl2));
+  const float b2 = fmaf(e20, bh0, fmaf(e21, bh1, e22 * bh2)) + fmaf(e20, bl0, fmaf(e21, bl1, e22 * bl2));
+  const float bn = fmaf(nh0, bh0, fmaf(nh1, bh1, nh2 * bh2));
+  const float d1 = fmaf(e10, ad0, fmaf(e11, ad1, e12 * ad2));
+  const float d2 = fmaf(e20, ad0, fmaf(e21, ad1, e22 * ad2));
+  const float dn = fmaf(nh0, ad0, fmaf(nh1, ad1, nh2 * ad2));
+  const float D = (g2 + fmaf(b1, b1, b2 * b2)) / (1.0f + bn);
+  const float iD = 1.0f / D;
+  const float iD2 = iD * iD;
+  const float a1 = -fmaf(b1, dn, d1 * D) * iD2;
+  const float a2 = -fmaf(b2, dn, d2 * D) * iD2;
+  amp[0] = ww * a1;  // U . e1
+  amp[1] = ww * a2;  // U . e2
+  amp[2] = sw * a1;  // V . e1
+  amp[3] = sw * a2;  // V . e2
+  return fabsf(th) <= tau_fast;  // false for NaN as well
+}
+
+// Shared memory: one raw particle tile (THREADS x 80 B, TMA destination) and
+// two record buffers.  FP32 variants: per record 3 float4 (values duplicated
+// for packed arithmetic); tensor-core variants: float2 dtau + 8 floats of
+// amplitude hi/lo parts.
+// Tensor-core variants also keep their per-chunk (second-level) sums in
+// shared memory: 16 floats per thread, one slot per thread and value.
+template <int THREADS, bool TC>
+struct Smem {
+  static constexpr size_t raw_bytes = (size_t)THREADS * kRecFields * sizeof(float);
+  static constexpr size_t rec_bytes = (size_t)THREADS * (TC ? 40 : 48);
+  static constexpr size_t l2_bytes = TC ? (size_t)THREADS * 16 * sizeof(float) : 0;
+  static constexpr size_t bytes = raw_bytes + 2 * rec_bytes + l2_bytes;
+};
+
+struct TileGeom {
+  int WT, NT, KT, d0, o0;
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const JobStatic& J, int tile, int threads) {
+  TileGeom g;
+  g.WT = J.wt;
+  g.NT = J.nt;
+  g.KT = threads / g.NT;
+  const int tile_d = tile / J.tiles_om;
+  g.d0 = tile_d * g.NT;
+  g.o0 = (tile - tile_d * J.tiles_om) * g.WT;
+  return g;
+}
+
+// Compensated (Kahan) add of x into sum with compensation cmp.
+__device__ __forceinline__ void kahan_add(float* sum, float* cmp, float x) {
+  const float y = __fsub_rn(x, *cmp);
+  const float tt = __fadd_rn(*sum, y);
+  *cmp = __fsub_rn(__fsub_rn(tt, *sum), y);
+  *sum = tt;
+}
+
+// Arrival counter of the bin tile; true for the last work item of this call.
+template <int THREADS>
+__device__ __forceinline__ bool last_arrival(const JobStatic& J, const JobCall& K, int tile,
+                                             int* s_flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&J.tile_cnt[tile], 1u);
+    *s_flag = (prev == (unsigned)(K.n_chunks - 1));
+    if (*s_flag) J.tile_cnt[tile] = 0u;  // ready for the next call
+    __threadfence();
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// Last arrival: for every bin of the tile, add the chunks' partials in chunk
+// order, rotate by e^{i omega tau_ref(n)} and add into the state (Kahan).
+template <int THREADS>
+__device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall& K, int tile) {
+  const TileGeom g = tile_geom(J, tile, THREADS);
+  const int nb = J.n_bins, n_om = J.n_omega;
+  for (int i = threadIdx.x; i < g.NT * g.WT; i += THREADS) {
+    const int dl = i / g.WT;
+    const int d = g.d0 + dl, o = g.o0 + (i - dl * g.WT);
+    if (d >= J.n_dir || o >= n_om) continue;
+    const int bin = d * n_om + o;
+    float s[kComps];
+#pragma unroll
+    for (int c = 0; c < kComps; ++c) s[c] = 0.0f;
+    for (int ch = 0; ch < K.n_chunks; ++ch) {
+      const float* pc = J.partials + (size_t)ch * kComps * nb;
+#pragma unroll
+      for (int c = 0; c < kComps; ++c) s[c] += __ldcg(&pc[(size_t)c * nb + bin]);
+    }
+    const double* nd = J.dirs + 3 * d;
+    const double tref = J.ref[3] - (nd[0] * J.ref[0] + nd[1] * J.ref[1] + nd[2] * J.ref[2]) * kInvC;
+    double psi = J.om_turns[o] * tref;
+    psi -= rint(psi);
+    float sp, cp;
+    sincospif(2.0f * (float)psi, &sp, &cp);
+    float* st = J.state;
+#pragma unroll
+    for (int c = 0; c < kComps; c += 2) {
+      const float re = s[c] * cp - s[c + 1] * sp;
+      const float im = s[c] * sp + s[c + 1] * cp;
+      kahan_add(&st[(size_t)c * nb + bin], &st[(size_t)(kComps + c) * nb + bin], re);
+      kahan_add(&st[(size_t)(c + 1) * nb + bin], &st[(size_t)(kComps + c + 1) * nb + bin], im);
+    }
+  }
+}
+
+// Phase of a frequency pair (packed) for one particle: returns radians in
+// (-pi, pi] + a tiny cross-term excess.
+__device__ __forceinline__ float2 phase2(float2 omh, float2 nomh, float2 wh, float2 wl, float2 th,
+                                         float2 tl) {
+  const float2 kMag = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23
+  const float2 kNegMag = make_float2(-12582912.0f, -12582912.0f);
+  const float2 k2Pi = make_float2(6.28318530717958647692f, 6.28318530717958647692f);
+  const float2 t0 = __ffma2_rn(nomh, th, kMag);  // 1.5*2^23 - rint(x)
+  const float2 q = __fadd2_rn(t0, kNegMag);       // -rint(x), exact
+  const float2 f0 = __ffma2_rn(omh, th, q);       // x - rint(x), one rounding
+  const float2 c1 = __fmul2_rn(wl, th);           // cross terms, radians
+  const float2 c2 = __ffma2_rn(wh, tl, c1);
+  return __ffma2_rn(f0, k2Pi, c2);
+}
+
+// Phase in FP64 (wide path): omega/2pi times the float-float dtau, reduced.
+__device__ __forceinline__ float phase_wide(double om_turns, float th, float tl) {
+  double x = om_turns * ((double)th + (double)tl);
+  x -= rint(x);
+  return (float)(x * 6.283185307179586);
+}
+
+// Loads one raw particle tile; thread 0 only.
+__device__ __forceinline__ void issue_tile(const JobStatic& J, long long k0, int KT, float* raw,
+                                           uint64_t* bar) {
+  tma_load_1d(raw, J.rec + (size_t)k0 * kRecFields, (uint32_t)KT * kRecFields * sizeof(float), bar);
+}
+
+// ------------------------------------------------------------ FP32 variant
+template <int THREADS, int W, int UNROLL>
+__device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCall& K, int tile,
+                                                 int chunk, unsigned char* __restrict__ smem,
+                                                 uint64_t* bar, uint32_t& phase, int* s_flag) {
+  constexpr int NP = W / 2;
+  using S = Smem<THREADS, false>;
+  float* raw = reinterpret_cast<float*>(smem);
+  const TileGeom g = tile_geom(J, tile, THREADS);
+  const int lanes_per_dir = g.WT / W;
+  const int my_dl = threadIdx.x / lanes_per_dir;
+  const int my_d_raw = g.d0 + my_dl;
+  const int my_d = min(my_d_raw, J.n_dir - 1);
+  const int om_first = g.o0 + (threadIdx.x - my_dl * lanes_per_dir) * W;
+  const int n_om = J.n_omega;
+  const int s1_dl = threadIdx.x / g.KT, s1_kk = threadIdx.x - s1_dl * g.KT;
+  const int s1_d = min(g.d0 + s1_dl, J.n_dir - 1);
+
+  float2 omh[NP], nomh[NP], wh[NP], wl[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int i0 = min(om_first + 2 * p, n_om - 1), i1 = min(om_first + 2 * p + 1, n_om - 1);
+    omh[p] = make_float2(__ldg(J.om_tab + i0), __ldg(J.om_tab + i1));
+    nomh[p] = make_float2(__ldg(J.om_tab + n_om + i0), __ldg(J.om_tab + n_om + i1));
+    wh[p] = make_float2(__ldg(J.om_tab + 2 * n_om + i0), __ldg(J.om_tab + 2 * n_om + i1));
+    wl[p] = make_float2(__ldg(J.om_tab + 3 * n_om + i0), __ldg(J.om_tab + 3 * n_om + i1));
+  }
+  float2 acc1[NP][kComps], acc2[NP][kComps];
+#pragma unroll
+  for (int p = 0; p < NP; ++p)
+#pragma unroll
+    for (int c = 0; c < kComps; ++c) acc1[p][c] = acc2[p][c] = make_float2(0.f, 0.f);
+
+  const long long k_begin = (long long)chunk * K.ck;
+  const long long k_end = min(k_begin + (long long)K.ck, K.n);
+  const int n_kt = (int)((k_end - k_begin + g.KT - 1) / g.KT);
+  // Whole tiles are copied: k_begin is a multiple of KT and the record buffer
+  // holds at least round_up(n, 256) particles, so every copy stays in bounds.
+  if (threadIdx.x == 0) issue_tile(J, k_begin, g.KT, raw, bar);
+  for (int it = 0; it < n_kt; ++it) {
+    const long long kt = k_begin + (long long)it * g.KT;
+    const int kn = (int)min((long long)g.KT, k_end - kt);
+    float4* rec = reinterpret_cast<float4*>(smem + S::raw_bytes + (size_t)(it & 1) * S::rec_bytes);
+    const bool landed = mbar_wait(bar, phase);
+    phase ^= 1u;
+    bool slow = false;
+    if (landed && s1_kk < kn) {
+      float th, tl, a[4];
+      slow = !compute_record(raw + s1_kk * kRecFields, J.dir_tab, J.n_dir, s1_d, J.tau_fast, th,
+                             tl, a);
+      float4* out = rec + (s1_kk * g.NT + s1_dl) * 3;
+      out[0] = make_float4(th, th, tl, tl);
+      out[1] = make_float4(a[0], a[0], a[1], a[1]);
+      out[2] = make_float4(a[2], a[2], a[3], a[3]);
+    }
+    const int flags = __syncthreads_or((slow ? 1 : 0) | (landed ? 0 : 2));
+    if (flags & 2) {
+      // The copy did not land within the bound: record it, wait (bounded) once
+      // more for that copy, and leave.
+      if (threadIdx.x == 0) {
+        atomicOr(J.status, ST_TIMEOUT);
+        mbar_wait(bar, phase ^ 1u);
+      }
+      return false;
+    }
+    if (threadIdx.x == 0 && it + 1 < n_kt) issue_tile(J, kt + g.KT, g.KT, raw, bar);
+    const float4* rc = rec + my_dl * 3;
+    if (!(flags & 1)) {
+#pragma unroll UNROLL
+      for (int kk = 0; kk < kn; ++kk) {
+        const float4 r0 = rc[kk * g.NT * 3 + 0];
+        const float4 r1 = rc[kk * g.NT * 3 + 1];
+        const float4 r2 = rc[kk * g.NT * 3 + 2];
+        const float2 th = make_float2(r0.x, r0.y), tl = make_float2(r0.z, r0.w);
+        const float2 aw1 = make_float2(r1.x, r1.y), aw2 = make_float2(r1.z, r1.w);
+        const float2 av1 = make_float2(r2.x, r2.y), av2 = make_float2(r2.z, r2.w);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const float2 ph = phase2(omh[p], nomh[p], wh[p], wl[p], th, tl);
+          const float2 cc = make_float2(cos_approx(ph.x), cos_approx(ph.y));
+          const float2 ss = make_float2(sin_approx(ph.x), sin_approx(ph.y));
+          acc1[p][0] = __ffma2_rn(aw1, cc, acc1[p][0]);
+          acc1[p][1] = __ffma2_rn(aw1, ss, acc1[p][1]);
+          acc1[p][2] = __ffma2_rn(aw2, cc, acc1[p][2]);
+          acc1[p][3] = __ffma2_rn(aw2, ss, acc1[p][3]);
+          acc1[p][4] = __ffma2_rn(av1, cc, acc1[p][4]);
+          acc1[p][5] = __ffma2_rn(av1, ss, acc1[p][5]);
+          acc1[p][6] = __ffma2_rn(av2, cc, acc1[p][6]);
+          acc1[p][7] = __ffma2_rn(av2, ss, acc1[p][7]);
+        }
+      }
+    } else {
+      // Wide path: some |dtau| exceed the fast range in this tile; the phase of
+      // every update is formed in FP64.
+      if (threadIdx.x == 0) atomicOr(J.status, ST_SLOW_PHASE);
+      double omt[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) omt[i] = J.om_turns[min(om_first + i, n_om - 1)];
+      for (int kk = 0; kk < kn; ++kk) {
+        const float4 r0 = rc[kk * g.NT * 3 + 0];
+        const float4 r1 = rc[kk * g.NT * 3 + 1];
+        const float4 r2 = rc[kk * g.NT * 3 + 2];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const float2 ph = make_float2(phase_wide(omt[2 * p], r0.x, r0.z),
+                                        phase_wide(omt[2 * p + 1], r0.x, r0.z));
+          const float2 cc = make_float2(cos_approx(ph.x), cos_approx(ph.y));
+          const float2 ss = make_float2(sin_approx(ph.x), sin_approx(ph.y));
+          acc1[p][0] = __ffma2_rn(make_float2(r1.x, r1.y), cc, acc1[p][0]);
+          acc1[p][1] = __ffma2_rn(make_float2(r1.x, r1.y), ss, acc1[p][1]);
+          acc1[p][2] = __ffma2_rn(make_float2(r1.z, r1.w), cc, acc1[p][2]);
+          acc1[p][3] = __ffma2_rn(make_float2(r1.z, r1.w), ss, acc1[p][3]);
+          acc1[p][4] = __ffma2_rn(make_float2(r2.x, r2.y), cc, acc1[p][4]);
+          acc1[p][5] = __ffma2_rn(make_float2(r2.x, r2.y), ss, acc1[p][5]);
+          acc1[p][6] = __ffma2_rn(make_float2(r2.z, r2.w), cc, acc1[p][6]);
+          acc1[p][7] = __ffma2_rn(make_float2(r2.z, r2.w), ss, acc1[p][7]);
+        }
+      }
+    }
+    // Two-level summation: the tile's sums join the chunk sums.
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+      for (int c = 0; c < kComps; ++c) {
+        acc2[p][c] = __fadd2_rn(acc2[p][c], acc1[p][c]);
+        acc1[p][c] = make_float2(0.f, 0.f);
+      }
+  }
+
+  // Partial sums of this work item.
+  const int nb = J.n_bins;
+  float* part = J.partials + (size_t)chunk * kComps * nb;
+  if (my_d_raw < J.n_dir) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int o = om_first + 2 * p + e;
+        if (o < n_om) {
+          const int bin = my_d * n_om + o;
+#pragma unroll
+          for (int c = 0; c < kComps; ++c)
+            part[(size_t)c * nb + bin] = e ? acc2[p][c].y : acc2[p][c].x;
+        }
+      }
+  }
+  if (last_arrival<THREADS>(J, K, tile, s_flag)) tile_epilogue<THREADS>(J, K, tile);
+  return true;
+}
+
+// ------------------------------------------------------ tensor-core variant
+__device__ __forceinline__ void mma_tf32(float d[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t tf32_hi(float x) { return __float_as_uint(x) & kTf32Mask; }
+
+// Splits a packed pair into TF32 hi bits and the exact FP32 rest.
+__device__ __forceinline__ void split_pair(float2 v, uint32_t& h0, uint32_t& h1, float2& lo) {
+  h0 = tf32_hi(v.x);
+  h1 = tf32_hi(v.y);
+  lo = __fadd2_rn(v, make_float2(-__uint_as_float(h0), -__uint_as_float(h1)));
+}
+
+// One 16-frequency x 8-particle MMA block: pA / pB are the phases of the
+// frequency rows (r, r+8) for particles (c, c+4) of the fragment layout.
+__device__ __forceinline__ void tc_block(float2 pA, float2 pB, uint32_t b0, uint32_t b1,
+                                         float dre[4], float dim[4]) {
+  const float2 cA = make_float2(cos_approx(pA.x), cos_approx(pA.y));
+  const float2 sA = make_float2(sin_approx(pA.x), sin_approx(pA.y));
+  const float2 cB = make_float2(cos_approx(pB.x), cos_approx(pB.y));
+  const float2 sB = make_float2(sin_approx(pB.x), sin_approx(pB.y));
+  uint32_t ca0, ca1, cb0, cb1, sa0, sa1, sb0, sb1;
+  float2 caL, cbL, saL, sbL;
+  split_pair(cA, ca0, ca1, caL);
+  split_pair(cB, cb0, cb1, cbL);
+  split_pair(sA, sa0, sa1, saL);
+  split_pair(sB, sb0, sb1, sbL);
+  // A fragment (m16n8k8 tf32): a0 = (row r, k c), a1 = (r+8, c), a2 = (r, c+4), a3 = (r+8, c+4)
+  mma_tf32(dre, ca0, ca1, cb0, cb1, b0, b1);
+  mma_tf32(dre, __float_as_uint(caL.x), __float_as_uint(caL.y), __float_as_uint(cbL.x),
+           __float_as_uint(cbL.y), b0, b1);
+  mma_tf32(dim, sa0, sa1, sb0, sb1, b0, b1);
+  mma_tf32(dim, __float_as_uint(saL.x), __float_as_uint(saL.y), __float_as_uint(sbL.x),
+           __float_as_uint(sbL.y), b0, b1);
+}
+
+// Warp layout: warp w handles direction d0 + w / (WT/32) and 32 frequencies
+// (two 16-row MMA blocks) starting at o0 + 32 (w % (WT/32)).
+template <int THREADS>
+__device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCall& K, int tile,
+                                                int chunk, unsigned char* __restrict__ smem,
+                                                uint64_t* bar, uint32_t& phase, int* s_flag) {
+  constexpr int NB = 2;  // 16-frequency blocks per warp
+  using S = Smem<THREADS, true>;
+  float* raw = reinterpret_cast<float*>(smem);
+  const TileGeom g = tile_geom(J, tile, THREADS);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = lane >> 2, c = lane & 3;
+  const int warps_per_dir = g.WT / (16 * NB);
+  const int my_dl = warp / warps_per_dir;
+  const int my_d_raw = g.d0 + my_dl;
+  const int my_d = min(my_d_raw, J.n_dir - 1);
+  const int o_warp = g.o0 + (warp - my_dl * warps_per_dir) * 16 * NB;
+  const int n_om = J.n_omega;
+  const int s1_dl = threadIdx.x / g.KT, s1_kk = threadIdx.x - s1_dl * g.KT;
+  const int s1_d = min(g.d0 + s1_dl, J.n_dir - 1);
+
+  float2 omh[NB], nomh[NB], wh[NB], wl[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int i0 = min(o_warp + 16 * b + r, n_om - 1), i1 = min(o_warp + 16 * b + r + 8, n_om - 1);
+    omh[b] = make_float2(__ldg(J.om_tab + i0), __ldg(J.om_tab + i1));
+    nomh[b] = make_float2(__ldg(J.om_tab + n_om + i0), __ldg(J.om_tab + n_om + i1));
+    wh[b] = make_float2(__ldg(J.om_tab + 2 * n_om + i0), __ldg(J.om_tab + 2 * n_om + i1));
+    wl[b] = make_float2(__ldg(J.om_tab + 3 * n_om + i0), __ldg(J.om_tab + 3 * n_om + i1));
+  }
+  float dre[NB][4], dim[NB][4];
+  // second-level sums: slot v of this thread at l2[v * THREADS + threadIdx.x]
+  float* l2 = reinterpret_cast<float*>(smem + S::raw_bytes + 2 * S::rec_bytes);
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      dre[b][e] = dim[b][e] = 0.0f;
+      l2[(b * 4 + e) * THREADS + threadIdx.x] = 0.0f;
+      l2[(NB * 4 + b * 4 + e) * THREADS + threadIdx.x] = 0.0f;
+    }
+
+  const long long k_begin = (long long)chunk * K.ck;
+  const long long k_end = min(k_begin + (long long)K.ck, K.n);
+  const int n_kt = (int)((k_end - k_begin + g.KT - 1) / g.KT);
+  if (threadIdx.x == 0) issue_tile(J, k_begin, g.KT, raw, bar);
+  for (int it = 0; it < n_kt; ++it) {
+    const long long kt = k_begin + (long long)it * g.KT;
+    const int kn = (int)min((long long)g.KT, k_end - kt);
+    unsigned char* recb = smem + S::raw_bytes + (size_t)(it & 1) * S::rec_bytes;
+    float2* tau2 = reinterpret_cast<float2*>(recb);                     // [NT][KT]
+    float* ampb = reinterpret_cast<float*>(recb + (size_t)THREADS * 8);  // [NT][KT][8]
+    const bool landed = mbar_wait(bar, phase);
+    phase ^= 1u;
+    bool slow = false;
+    if (landed) {
+      float th = 0.f, tl = 0.f, a[4] = {0.f, 0.f, 0.f, 0.f};
+      if (s1_kk < kn)
+        slow = !compute_record(raw + s1_kk * kRecFields, J.dir_tab, J.n_dir, s1_d, J.tau_fast, th,
+                               tl, a);
+      // Particles past kn are zero padding of the last 8-particle MMA step.
+      const int slot = s1_dl * g.KT + s1_kk;
+      tau2[slot] = make_float2(th, tl);
+      float4* ap = reinterpret_cast<float4*>(ampb + (size_t)slot * 8);
+      const uint32_t h0 = tf32_hi(a[0]), h1 = tf32_hi(a[1]), h2 = tf32_hi(a[2]), h3 = tf32_hi(a[3]);
+      ap[0] = make_float4(__uint_as_float(h0), __uint_as_float(h1), __uint_as_float(h2),
+                          __uint_as_float(h3));
+      ap[1] = make_float4(a[0] - __uint_as_float(h0), a[1] - __uint_as_float(h1),
+                          a[2] - __uint_as_float(h2), a[3] - __uint_as_float(h3));
+    }
+    const int flags = __syncthreads_or((slow ? 1 : 0) | (landed ? 0 : 2));
+    if (flags & 2) {
+      if (threadIdx.x == 0) {
+        atomicOr(J.status, ST_TIMEOUT);
+        mbar_wait(bar, phase ^ 1u);
+      }
+      return false;
+    }
+    if (threadIdx.x == 0 && it + 1 < n_kt) issue_tile(J, kt + g.KT, g.KT, raw, bar);
+    const float2* tw = tau2 + my_dl * g.KT;
+    const float* aw = ampb + (size_t)my_dl * g.KT * 8;
+    const int kn8 = (kn + 7) & ~7;
+    if (!(flags & 1)) {
+#pragma unroll 2
+      for (int kk = 0; kk < kn8; kk += 8) {
+        const float2 tA = tw[kk + c], tB = tw[kk + c + 4];
+        const uint32_t b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
+        const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
+        const float2 thA = make_float2(tA.x, tA.x), tlA = make_float2(tA.y, tA.y);
+        const float2 thB = make_float2(tB.x, tB.x), tlB = make_float2(tB.y, tB.y);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const float2 pA = phase2(omh[b], nomh[b], wh[b], wl[b], thA, tlA);
+          const float2 pB = phase2(omh[b], nomh[b], wh[b], wl[b], thB, tlB);
+          tc_block(pA, pB, b0, b1, dre[b], dim[b]);
+        }
+      }
+    } else {
+      if (threadIdx.x == 0) atomicOr(J.status, ST_SLOW_PHASE);
+      double omt[NB][2];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        omt[b][0] = J.om_turns[min(o_warp + 16 * b + r, n_om - 1)];
+        omt[b][1] = J.om_turns[min(o_warp + 16 * b + r + 8, n_om - 1)];
+      }
+      for (int kk = 0; kk < kn8; kk += 8) {
+        const float2 tA = tw[kk + c], tB = tw[kk + c + 4];
+        const uint32_t b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
+        const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const float2 pA = make_float2(phase_wide(omt[b][0], tA.x, tA.y), phase_wide(omt[b][1], tA.x, tA.y));
+          const float2 pB = make_float2(phase_wide(omt[b][0], tB.x, tB.y), phase_wide(omt[b][1], tB.x, tB.y));
+          tc_block(pA, pB, b0, b1, dre[b], dim[b]);
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        l2[(b * 4 + e) * THREADS + threadIdx.x] += dre[b][e];
+        l2[(NB * 4 + b * 4 + e) * THREADS + threadIdx.x] += dim[b][e];
+        dre[b][e] = dim[b][e] = 0.0f;
+      }
+  }
+
+  // The D fragment holds rows (r, r+8) and columns (2c, 2c+1); columns 0-3 are
+  // the hi parts of (U.e1, U.e2, V.e1, V.e2), columns 4-7 the lo parts: lane c
+  // (c < 2) adds lane c+2's values.
+  const int nb = J.n_bins;
+  float* part = J.partials + (size_t)chunk * kComps * nb;
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float lre = l2[(b * 4 + e) * THREADS + threadIdx.x];
+      const float lim = l2[(NB * 4 + b * 4 + e) * THREADS + threadIdx.x];
+      const float re = lre + __shfl_xor_sync(0xffffffffu, lre, 2);
+      const float im = lim + __shfl_xor_sync(0xffffffffu, lim, 2);
+      const int o = o_warp + 16 * b + r + ((e >> 1) << 3);
+      const int j = 2 * c + (e & 1);  // amplitude column
+      if (c < 2 && my_d_raw < J.n_dir && o < n_om) {
+        const int bin = my_d * n_om + o;
+        part[(size_t)(2 * j) * nb + bin] = re;
+        part[(size_t)(2 * j + 1) * nb + bin] = im;
+      }
+    }
+  if (last_arrival<THREADS>(J, K, tile, s_flag)) tile_epilogue<THREADS>(J, K, tile);
+  return true;
+}
+
+template <int THREADS, int W, int MINB, bool TC>
+__global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ long long s_item[2];
+  __shared__ int s_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0u;
+  int buf = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_item[buf] = (long long)atomicAdd(a.item_counter, 1ULL);
+    __syncthreads();
+    const long long item = s_item[buf];
+    buf ^= 1;
+    if (item >= a.n_items) return;
+    const int j = find_job(a, item);
+    const JobStatic& J = a.js[j];
+    const JobCall K = a.use_inline ? a.inline_call : a.jc[j];
+    const long long local = item - K.item_begin;
+    const int tile = (int)(local % J.n_tiles);
+    const int chunk = (int)(local / J.n_tiles);
+    bool ok;
+    if constexpr (TC) ok = process_item_tc<THREADS>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
+    else ok = process_item_fma<THREADS, W, 2>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
+    if (!ok) return;
+  }
+}
+
+template <int T, int W, int MINB, bool TC>
+cudaError_t launch_acc(const LaunchArgs& a, int grid, cudaStream_t s) {
+  const size_t smem = Smem<T, TC>::bytes;
+  static bool attr_set = false;  // the opt-in is per kernel and idempotent
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  accumulate_kernel<T, W, MINB, TC><<<grid, T, smem, s>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int T, int W, int MINB, bool TC>
+int blocks_per_sm() {
+  int nb = 0;
+  const size_t smem = Smem<T, TC>::bytes;
+  cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accumulate_kernel<T, W, MINB, TC>, T,
+                                                    smem) != cudaSuccess ||
+      nb < 1)
+    nb = 1;
+  return nb;
+}
+
+}  // namespace
+
+// Variants (rad_impl.h: variant_info): 0 FP32 256x2, 1 FP32 256x4, 2 FP32 128x2,
+// 3 tensor-core 256 (3 CTAs/SM), 4 tensor-core 256 (4 CTAs/SM), 5 FP32 256x2 (4 CTAs/SM).
+size_t accumulate_smem_bytes(int variant) {
+  switch (variant) {
+    case 2: return Smem<128, false>::bytes;
+    case 3:
+    case 4: return Smem<256, true>::bytes;
+    default: return Smem<256, false>::bytes;
+  }
+}
+
+int accumulate_blocks_per_sm(int variant) {
+  static int cached[kNumVariants] = {};
+  if (variant < 0 || variant >= kNumVariants) variant = 0;
+  if (cached[variant] == 0) {
+    switch (variant) {
+      case 1: cached[1] = blocks_per_sm<256, 4, 2, false>(); break;
+      case 2: cached[2] = blocks_per_sm<128, 2, 6, false>(); break;
+      case 3: cached[3] = blocks_per_sm<256, 1, 3, true>(); break;
+      case 4: cached[4] = blocks_per_sm<256, 1, 4, true>(); break;
+      case 5: cached[5] = blocks_per_sm<256, 2, 4, false>(); break;
+      default: cached[0] = blocks_per_sm<256, 2, 3, false>(); break;
+    }
+  }
+  return cached[variant];
+}
+
+cudaError_t launch_accumulate(int variant, const LaunchArgs& a, int grid, cudaStream_t s) {
+  switch (variant) {
+    case 1: return launch_acc<256, 4, 2, false>(a, grid, s);
+    case 2: return launch_acc<128, 2, 6, false>(a, grid, s);
+    case 3: return launch_acc<256, 1, 3, true>(a, grid, s);
+    case 4: return launch_acc<256, 1, 4, true>(a, grid, s);
+    case 5: return launch_acc<256, 2, 4, false>(a, grid, s);
+    default: return launch_acc<256, 2, 3, false>(a, grid, s);
+  }
+}
+
+}  // namespace radimpl

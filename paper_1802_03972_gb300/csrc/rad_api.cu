@@ -282,7 +282,7 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
   if ((long long)n_omega * n_dir > 0x7fffffffLL) return RAD_EINVAL;
   if (prec != RAD_PREC_MIXED && prec != RAD_PREC_FP64) return RAD_EINVAL;
   if (ff.kind < RAD_FF_POINT || ff.kind > RAD_FF_GAUSS || !(ff.width >= 0.0) ||
-      !isfinite(ff.width))
+      !isfinite(ff.width) || (ff.flags & ~RAD_FF_3D) != 0)
     return RAD_EINVAL;
   for (int i = 0; i < n_omega; ++i)
     if (!(omega[i] > 0.0) || !isfinite(omega[i])) return RAD_EINVAL;
@@ -467,7 +467,8 @@ rad_status rad_sync(rad_ctx* c) {
 rad_status rad_spectrum_ff(rad_ctx* c, rad_ff ff, double* coh, double* inc, double* tot) {
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
-  if (ff.kind < RAD_FF_POINT || ff.kind > RAD_FF_GAUSS || !(ff.width >= 0.0) || !isfinite(ff.width))
+  if (ff.kind < RAD_FF_POINT || ff.kind > RAD_FF_GAUSS || !(ff.width >= 0.0) ||
+      !isfinite(ff.width) || (ff.flags & ~RAD_FF_3D) != 0)
     return fail(c, RAD_EINVAL);
   double* outs[3] = {coh, inc, tot};
   double* dev_out[3];
@@ -477,8 +478,8 @@ rad_status rad_spectrum_ff(rad_ctx* c, rad_ff ff, double* coh, double* inc, doub
     dev_out[i] = outs[i] ? (host[i] ? c->d_spec + (size_t)i * c->n_bins : outs[i]) : nullptr;
   }
   rad_status s = cuda_check(c, launch_readout(c->d_state, c->prec == RAD_PREC_MIXED, c->d_state64,
-                                              c->n_omega, c->n_bins, c->d_omega, ff, dev_out[0],
-                                              dev_out[1], dev_out[2], c->stream));
+                                              c->n_omega, c->n_bins, c->d_omega, c->d_dirs, ff,
+                                              dev_out[0], dev_out[1], dev_out[2], c->stream));
   if (s != RAD_OK) return s;
   for (int i = 0; i < 3; ++i) {
     if (!host[i]) continue;

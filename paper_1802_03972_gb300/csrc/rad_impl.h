@@ -85,11 +85,16 @@ struct Variant {
   int threads;
   int w;  // frequencies per thread
 };
-constexpr int kNumVariants = 3;
+// 0-2, 5: FP32-FMA accumulation, w frequencies per thread;
+// 3-4: tensor-core accumulation, a warp covers 32 frequencies (w = 1 in the
+// tiling rules: bins per tile = threads x w, frequency tiles multiples of 32 w).
+constexpr int kNumVariants = 6;
 inline Variant variant_info(int v) {
   switch (v) {
     case 1: return {256, 4};
     case 2: return {128, 2};
+    case 3:
+    case 4: return {256, 1};
     default: return {256, 2};
   }
 }
@@ -100,8 +105,8 @@ cudaError_t launch_accumulate(int variant, const LaunchArgs& a, int grid, cudaSt
 int accumulate_blocks_per_sm(int variant);
 size_t accumulate_smem_bytes(int variant);
 cudaError_t launch_readout(const float* state, int mixed, const double* state64, int n_omega,
-                           int n_bins, const double* omega, rad_ff ff, double* coh, double* inc,
-                           double* tot, cudaStream_t s);
+                           int n_bins, const double* omega, const double* dirs, rad_ff ff,
+                           double* coh, double* inc, double* tot, cudaStream_t s);
 cudaError_t launch_fp64(const double* omega, const double* dirs, int n_omega, int n_dir,
                         long long n, const double* r, const double* beta, const double* bdot,
                         const double* w, double t, double dt, double* state64, int* status,

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "librad.so")
 
 RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_EDATA, RAD_ETIMEOUT, RAD_EBUSY, RAD_ESTATE = range(8)
 FF_POINT, FF_CIC, FF_TSC, FF_QSC, FF_GAUSS = range(5)
+FF_3D = 1  # rad_ff.flags: box shapes as axis-aligned 3-D products
 PREC_MIXED, PREC_FP64 = 0, 1
 STATUS_NAMES = ["RAD_OK", "RAD_EINVAL", "RAD_ENOMEM", "RAD_ECUDA", "RAD_EDATA", "RAD_ETIMEOUT",
                 "RAD_EBUSY", "RAD_ESTATE"]
@@ -45,7 +46,7 @@ class RadError(RuntimeError):
 
 
 class rad_ff(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("width", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int32), ("flags", ctypes.c_int32), ("width", ctypes.c_double)]
 
 
 class rad_tile(ctypes.Structure):
@@ -182,14 +183,15 @@ class Context:
     """One spectrum job: rad_create / rad_accumulate / rad_spectrum."""
 
     def __init__(self, omega, dirs, ff_kind: int = FF_POINT, ff_width: float = 0.0,
-                 prec: int = PREC_MIXED, stream=None):
+                 prec: int = PREC_MIXED, stream=None, ff_flags: int = 0):
         lib = load()
+        self._ff_flags = int(ff_flags)
         self.omega = _f64_host(omega).ravel()
         self.dirs = _f64_host(dirs).reshape(-1, 3)
         self.n_omega, self.n_dir = self.omega.shape[0], self.dirs.shape[0]
         h = ctypes.c_void_p()
         _check(lib.rad_create(self.omega.ctypes.data, self.n_omega, self.dirs.ctypes.data,
-                              self.n_dir, rad_ff(ff_kind, 0, ff_width), prec,
+                              self.n_dir, rad_ff(ff_kind, self._ff_flags, ff_width), prec,
                               _stream_handle(stream), ctypes.byref(h)), "rad_create")
         self._h = h
         self._lib = lib
@@ -234,7 +236,8 @@ class Context:
         if ff is None:
             st = self._lib.rad_spectrum(self._h, *ptrs)
         else:
-            st = self._lib.rad_spectrum_ff(self._h, rad_ff(int(ff[0]), 0, float(ff[1])), *ptrs)
+            flags = int(ff[2]) if len(ff) > 2 else 0
+            st = self._lib.rad_spectrum_ff(self._h, rad_ff(int(ff[0]), flags, float(ff[1])), *ptrs)
         _check(st, "rad_spectrum")
         return out
 

@@ -59,5 +59,5 @@ def oracle_run(wl: inputs.Workload, steps, bins=None):
 
 
 def spectra_grid(acc: oracle.Accumulator, wl: inputs.Workload, ff=None) -> dict:
-    sp = acc.spectra(*(ff or (None, None)))
+    sp = acc.spectra(*(ff or (None, None, None)))
     return {k: v.reshape(wl.dirs.shape[0], wl.omega.shape[0]) for k, v in sp.items()}

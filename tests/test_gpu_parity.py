@@ -64,7 +64,7 @@ def small_lwfa(n=2000, n_omega=100, n_side=8, seed=21):
     return wl
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_lwfa_small_full_grid_all_variants(variant):
     """LWFA-shaped bunch with weights, Gaussian form factor, ragged particle count
     (2000 = 31 x 64 + 16) and ragged frequency tile (100 of 128), 20 steps."""
@@ -84,6 +84,18 @@ def test_lwfa_readout_with_other_shapes():
                         (oracle.FF_POINT, 0.0)):
         ref = spectra_grid(acc, wl, (kind, width))
         check(ctx, ref, ff=(kind, width), parts=("tot", "coh") + (("inc",) if kind else ()))
+
+
+def test_readout_3d_box_form_factor():
+    """Axis-aligned 3-D box shapes (RAD_FF_3D): the form factor depends on the
+    direction; oblique directions over a wide cone so the product differs."""
+    wl = small_lwfa(n=400, n_omega=64, n_side=1)
+    wl.dirs = inputs.dirs_grid(0.6, 3, 3)  # +-0.6 rad: strongly oblique directions
+    acc = oracle_run(wl, range(4))
+    ctx = gpu_run(wl, range(4))
+    for kind, width in ((oracle.FF_CIC, 0.3e-6), (oracle.FF_TSC, 0.2e-6)):
+        ref = spectra_grid(acc, wl, (kind, width, oracle.FF_3D))
+        check(ctx, ref, ff=(kind, width, rad.FF_3D))
 
 
 def test_lwfa_full_size_sampled_rows():

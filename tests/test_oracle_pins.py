@@ -441,3 +441,58 @@ def test_energy_integral_equals_lienard_power():
     gamma = 1.0 / np.sqrt(1 - beta * beta)
     lienard = np.sum(qe**2 * gamma**6 * bdot**2 / (6 * math.pi * eps0 * C)) * h
     assert energy == pytest.approx(lienard, rel=1e-6, abs=0)
+
+
+# ------------------------------------------- direction-dependent box shapes
+def test_form_factor_3d_reduces_to_table1_along_axes():
+    """The axis-aligned 3-D box product equals the 1-D Table 1 form along a
+    coordinate axis (the other factors are sinc(0) = 1) and differs off-axis."""
+    width = 0.2e-6
+    for kind in (oracle.FF_CIC, oracle.FF_TSC, oracle.FF_QSC):
+        for om in (3e14, 2e15, 9e15):
+            f1 = oracle.form_factor(kind, width, om)[0]
+            for axis in np.eye(3):
+                assert oracle.form_factor_dir(kind, oracle.FF_3D, width, om, axis) == f1
+            n = np.array([1.0, 2.0, 3.0]) / math.sqrt(14.0)
+            f3 = oracle.form_factor_dir(kind, oracle.FF_3D, width, om, n)
+            want = np.prod([oracle.form_factor(kind, width, om * c)[0] for c in n])
+            assert f3 == pytest.approx(want, rel=1e-14, abs=0)
+    # the isotropic Gaussian ignores the flag
+    n = np.array([0.6, 0.0, 0.8])
+    assert oracle.form_factor_dir(oracle.FF_GAUSS, oracle.FF_3D, 0.1e-6, 1e15, n) == \
+        oracle.form_factor(oracle.FF_GAUSS, 0.1e-6, 1e15)[0]
+
+
+@pytest.mark.parametrize("shape", ["CIC", "TSC"])
+def test_brute_force_3d_box_offsets_oblique_direction(shape):
+    """Electrons offset by an axis-aligned 3-D box distribution, seen along an
+    oblique direction: the Monte-Carlo mean of |sum|^2 matches the 3-D product
+    form factor (Sec. 3.2 with rho = rho(x) rho(y) rho(z)) and not the 1-D form."""
+    rng = np.random.default_rng(21)
+    traj, times, dt = _short_helix(n_steps=10)
+    width = 0.15e-6
+    n = np.array([0.5, -0.6, math.sqrt(1 - 0.25 - 0.36)])
+    om = {"CIC": 3.0, "TSC": 2.0}[shape] * 2 * C / width  # omega Delta / 2c along a unit axis
+    kind = KIND[shape]
+    w = 12
+    R = 1500
+    macro = oracle.Accumulator([om], [n], kind, width, oracle.FF_3D)
+    for t in times:
+        r, b, bd = traj(t)
+        macro.accumulate(r, b, bd, [float(w)], t, dt)
+    want = macro.spectra()["tot"][0]
+    want_1d = macro.spectra(ff_flags=0)["tot"][0]
+    m = {"CIC": 1, "TSC": 2}[shape]
+    offs = [sum(rng.uniform(-0.5, 0.5, (3, w)) for _ in range(m)) * width for _ in range(R)]
+    el = None
+    for t in times:
+        r, b, bd = traj(t)
+        rr = np.concatenate([r[:, None] + o for o in offs], 1)
+        k = rr.shape[1]
+        el = oracle.accumulate_particles([om], [n], rr, np.repeat(b[:, None], k, 1),
+                                         np.repeat(bd[:, None], k, 1), t, dt, el)
+    z = oracle.complex_particles(el)[:, 0, :].reshape(R, w, 3).sum(axis=1)
+    vals = oracle.k0() * np.sum(np.abs(z) ** 2, axis=1)
+    mean, se = vals.mean(), vals.std(ddof=1) / math.sqrt(R)
+    assert abs(mean - want) <= 5 * se, (mean / want, se / want)
+    assert abs(mean - want_1d) > 5 * se  # the direction dependence is resolved
