@@ -80,9 +80,18 @@ typedef enum {
  * depends on omega only (Table 1 with n along one axis, as printed).  The
  * Gaussian is isotropic and ignores the flag. */
 #define RAD_FF_3D 1
+/* RAD_FF_LITERAL (at rad_create only): also accumulate the paper's literal
+ * in-situ sum P = sum_t sum_k F_k(omega) dt A_k chi_k with the per-particle
+ * weight F_k = sqrt(w_k + (w_k^2 - w_k) f(omega)^2) (Eq. 13 with Eq. 12), read
+ * out by rad_spectrum_literal as K0 |P|^2.  For equal weights, or one
+ * macro-particle, it equals the split total; otherwise it differs by the
+ * cross-particle terms the split estimate treats as incoherent.  Costs one more
+ * sqrt per amplitude update; such contexts run on their own (not in
+ * rad_batch or the server). */
+#define RAD_FF_LITERAL 2
 typedef struct {
   int32_t kind;  /* rad_ff_kind */
-  int32_t flags; /* 0 or RAD_FF_3D */
+  int32_t flags; /* 0, RAD_FF_3D, RAD_FF_LITERAL or both */
   double width;
 } rad_ff;
 
@@ -133,6 +142,27 @@ rad_status rad_spectrum(rad_ctx* ctx, double* coherent, double* incoherent, doub
  * out of the same accumulation). */
 rad_status rad_spectrum_ff(rad_ctx* ctx, rad_ff ff, double* coherent, double* incoherent,
                            double* total);
+
+/* In-situ coupling to a particle pusher that provides positions and velocities
+ * each PIC step but not beta_dot (the inner sum of Eq. 13 is evaluated in situ
+ * at every step, Sec. 3.3).  rad_push_step hands over step j: r_j, beta_j, w_j
+ * at time t_j with step length dt_j (host or device arrays, copied).  The
+ * context keeps the last two steps on the device; when step j+1 arrives it
+ * accumulates step j with the central difference
+ *   beta_dot_j = (beta_{j+1} - beta_{j-1}) / (t_{j+1} - t_{j-1}),
+ * second-order accurate (the first step uses the forward difference
+ * (beta_1 - beta_0) / (t_1 - t_0)).  rad_push_flush accumulates the last held
+ * step with the backward difference and clears the history.  Macro-particle k
+ * must be the same in every step (same count and order); RAD_EINVAL otherwise.
+ * Needs 192 bytes of device memory per macro-particle. */
+rad_status rad_push_step(rad_ctx* ctx, int64_t n, const double* r, const double* beta,
+                         const double* w, double t, double dt);
+rad_status rad_push_flush(rad_ctx* ctx);
+
+/* rad_spectrum_literal - the paper's literal spectrum K0 |P|^2 ([n_dir][n_omega]
+ * doubles, host or device) of a context created with RAD_FF_LITERAL, with the
+ * creation shape.  RAD_ESTATE for other contexts.  Synchronises the stream. */
+rad_status rad_spectrum_literal(rad_ctx* ctx, double* literal);
 
 /* rad_sync - wait for the context's queued work; report RAD_EDATA / errors. */
 rad_status rad_sync(rad_ctx* ctx);

@@ -118,10 +118,11 @@ __device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
 // amplitude hi/lo parts.
 // Tensor-core variants also keep their per-chunk (second-level) sums in
 // shared memory: 16 floats per thread, one slot per thread and value.
-template <int THREADS, bool TC>
+// The literal variant adds a fourth float4 per record: (w - 1) duplicated.
+template <int THREADS, bool TC, bool LIT = false>
 struct Smem {
   static constexpr size_t raw_bytes = (size_t)THREADS * kRecFields * sizeof(float);
-  static constexpr size_t rec_bytes = (size_t)THREADS * (TC ? 40 : 48);
+  static constexpr size_t rec_bytes = (size_t)THREADS * (TC ? 40 : (LIT ? 64 : 48));
   static constexpr size_t l2_bytes = TC ? (size_t)THREADS * 16 * sizeof(float) : 0;
   static constexpr size_t bytes = raw_bytes + 2 * rec_bytes + l2_bytes;
 };
@@ -198,7 +199,29 @@ __device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall&
       kahan_add(&st[(size_t)c * nb + bin], &st[(size_t)(kComps + c) * nb + bin], re);
       kahan_add(&st[(size_t)(c + 1) * nb + bin], &st[(size_t)(kComps + c + 1) * nb + bin], im);
     }
+    if (J.literal) {
+      float p[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int ch = 0; ch < K.n_chunks; ++ch) {
+        const float* pc = J.partials_p + (size_t)ch * 4 * nb;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p[c] += __ldcg(&pc[(size_t)c * nb + bin]);
+      }
+      float* sp_ = J.state_p;
+#pragma unroll
+      for (int c = 0; c < 4; c += 2) {
+        const float re = p[c] * cp - p[c + 1] * sp;
+        const float im = p[c] * sp + p[c + 1] * cp;
+        kahan_add(&sp_[(size_t)c * nb + bin], &sp_[(size_t)(4 + c) * nb + bin], re);
+        kahan_add(&sp_[(size_t)(c + 1) * nb + bin], &sp_[(size_t)(4 + c + 1) * nb + bin], im);
+      }
+    }
   }
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Phase of a frequency pair (packed) for one particle: returns radians in
@@ -230,12 +253,16 @@ __device__ __forceinline__ void issue_tile(const JobStatic& J, long long k0, int
 }
 
 // ------------------------------------------------------------ FP32 variant
-template <int THREADS, int W, int UNROLL>
+// LIT: also the paper's literal sum P_i += sqrt(w) dt a_i g e^{i phi} with
+// g = sqrt(1 + (w - 1) f(omega)^2), i.e. F_k(omega) dt a_i (Eq. 13 with Eq. 12).
+template <int THREADS, int W, int UNROLL, bool LIT = false>
 __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCall& K, int tile,
                                                  int chunk, unsigned char* __restrict__ smem,
                                                  uint64_t* bar, uint32_t& phase, int* s_flag) {
   constexpr int NP = W / 2;
-  using S = Smem<THREADS, false>;
+  constexpr int REC = LIT ? 4 : 3;                 // float4 per record
+  constexpr int NC = kComps + (LIT ? 4 : 0);       // accumulated components per frequency
+  using S = Smem<THREADS, false, LIT>;
   float* raw = reinterpret_cast<float*>(smem);
   const TileGeom g = tile_geom(J, tile, THREADS);
   const int lanes_per_dir = g.WT / W;
@@ -256,11 +283,20 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
     wh[p] = make_float2(__ldg(J.om_tab + 2 * n_om + i0), __ldg(J.om_tab + 2 * n_om + i1));
     wl[p] = make_float2(__ldg(J.om_tab + 3 * n_om + i0), __ldg(J.om_tab + 3 * n_om + i1));
   }
-  float2 acc1[NP][kComps], acc2[NP][kComps];
+  float2 f2[NP];
+  if (LIT) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int i0 = min(om_first + 2 * p, n_om - 1), i1 = min(om_first + 2 * p + 1, n_om - 1);
+      f2[p] = make_float2(__ldg(J.f2_tab + i0), __ldg(J.f2_tab + i1));
+    }
+  }
+  float2 acc1[NP][NC], acc2[NP][NC];
 #pragma unroll
   for (int p = 0; p < NP; ++p)
 #pragma unroll
-    for (int c = 0; c < kComps; ++c) acc1[p][c] = acc2[p][c] = make_float2(0.f, 0.f);
+    for (int c = 0; c < NC; ++c) acc1[p][c] = acc2[p][c] = make_float2(0.f, 0.f);
+  const float2 kOne = make_float2(1.0f, 1.0f);
 
   const long long k_begin = (long long)chunk * K.ck;
   const long long k_end = min(k_begin + (long long)K.ck, K.n);
@@ -279,10 +315,14 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
       float th, tl, a[4];
       slow = !compute_record(raw + s1_kk * kRecFields, J.dir_tab, J.n_dir, s1_d, J.tau_fast, th,
                              tl, a);
-      float4* out = rec + (s1_kk * g.NT + s1_dl) * 3;
+      float4* out = rec + (s1_kk * g.NT + s1_dl) * REC;
       out[0] = make_float4(th, th, tl, tl);
       out[1] = make_float4(a[0], a[0], a[1], a[1]);
       out[2] = make_float4(a[2], a[2], a[3], a[3]);
+      if (LIT) {
+        const float wm1 = raw[s1_kk * kRecFields + 18];
+        out[REC - 1] = make_float4(wm1, wm1, 0.f, 0.f);
+      }
     }
     const int flags = __syncthreads_or((slow ? 1 : 0) | (landed ? 0 : 2));
     if (flags & 2) {
@@ -295,13 +335,13 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
       return false;
     }
     if (threadIdx.x == 0 && it + 1 < n_kt) issue_tile(J, kt + g.KT, g.KT, raw, bar);
-    const float4* rc = rec + my_dl * 3;
+    const float4* rc = rec + my_dl * REC;
     if (!(flags & 1)) {
 #pragma unroll UNROLL
       for (int kk = 0; kk < kn; ++kk) {
-        const float4 r0 = rc[kk * g.NT * 3 + 0];
-        const float4 r1 = rc[kk * g.NT * 3 + 1];
-        const float4 r2 = rc[kk * g.NT * 3 + 2];
+        const float4 r0 = rc[kk * g.NT * REC + 0];
+        const float4 r1 = rc[kk * g.NT * REC + 1];
+        const float4 r2 = rc[kk * g.NT * REC + 2];
         const float2 th = make_float2(r0.x, r0.y), tl = make_float2(r0.z, r0.w);
         const float2 aw1 = make_float2(r1.x, r1.y), aw2 = make_float2(r1.z, r1.w);
         const float2 av1 = make_float2(r2.x, r2.y), av2 = make_float2(r2.z, r2.w);
@@ -318,6 +358,16 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
           acc1[p][5] = __ffma2_rn(av1, ss, acc1[p][5]);
           acc1[p][6] = __ffma2_rn(av2, cc, acc1[p][6]);
           acc1[p][7] = __ffma2_rn(av2, ss, acc1[p][7]);
+          if (LIT) {
+            const float4 r3 = rc[kk * g.NT * REC + REC - 1];
+            const float2 g2 = __ffma2_rn(make_float2(r3.x, r3.y), f2[p], kOne);
+            const float2 gg = make_float2(sqrt_approx(g2.x), sqrt_approx(g2.y));
+            const float2 pv1 = __fmul2_rn(av1, gg), pv2 = __fmul2_rn(av2, gg);
+            acc1[p][NC - 4] = __ffma2_rn(pv1, cc, acc1[p][NC - 4]);
+            acc1[p][NC - 3] = __ffma2_rn(pv1, ss, acc1[p][NC - 3]);
+            acc1[p][NC - 2] = __ffma2_rn(pv2, cc, acc1[p][NC - 2]);
+            acc1[p][NC - 1] = __ffma2_rn(pv2, ss, acc1[p][NC - 1]);
+          }
         }
       }
     } else {
@@ -328,9 +378,9 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
 #pragma unroll
       for (int i = 0; i < W; ++i) omt[i] = J.om_turns[min(om_first + i, n_om - 1)];
       for (int kk = 0; kk < kn; ++kk) {
-        const float4 r0 = rc[kk * g.NT * 3 + 0];
-        const float4 r1 = rc[kk * g.NT * 3 + 1];
-        const float4 r2 = rc[kk * g.NT * 3 + 2];
+        const float4 r0 = rc[kk * g.NT * REC + 0];
+        const float4 r1 = rc[kk * g.NT * REC + 1];
+        const float4 r2 = rc[kk * g.NT * REC + 2];
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
           const float2 ph = make_float2(phase_wide(omt[2 * p], r0.x, r0.z),
@@ -345,6 +395,17 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
           acc1[p][5] = __ffma2_rn(make_float2(r2.x, r2.y), ss, acc1[p][5]);
           acc1[p][6] = __ffma2_rn(make_float2(r2.z, r2.w), cc, acc1[p][6]);
           acc1[p][7] = __ffma2_rn(make_float2(r2.z, r2.w), ss, acc1[p][7]);
+          if (LIT) {
+            const float4 r3 = rc[kk * g.NT * REC + REC - 1];
+            const float2 g2 = __ffma2_rn(make_float2(r3.x, r3.y), f2[p], kOne);
+            const float2 gg = make_float2(sqrt_approx(g2.x), sqrt_approx(g2.y));
+            const float2 pv1 = __fmul2_rn(make_float2(r2.x, r2.y), gg);
+            const float2 pv2 = __fmul2_rn(make_float2(r2.z, r2.w), gg);
+            acc1[p][NC - 4] = __ffma2_rn(pv1, cc, acc1[p][NC - 4]);
+            acc1[p][NC - 3] = __ffma2_rn(pv1, ss, acc1[p][NC - 3]);
+            acc1[p][NC - 2] = __ffma2_rn(pv2, cc, acc1[p][NC - 2]);
+            acc1[p][NC - 1] = __ffma2_rn(pv2, ss, acc1[p][NC - 1]);
+          }
         }
       }
     }
@@ -352,7 +413,7 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
-      for (int c = 0; c < kComps; ++c) {
+      for (int c = 0; c < NC; ++c) {
         acc2[p][c] = __fadd2_rn(acc2[p][c], acc1[p][c]);
         acc1[p][c] = make_float2(0.f, 0.f);
       }
@@ -372,6 +433,12 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
 #pragma unroll
           for (int c = 0; c < kComps; ++c)
             part[(size_t)c * nb + bin] = e ? acc2[p][c].y : acc2[p][c].x;
+          if (LIT) {
+            float* pp = J.partials_p + (size_t)chunk * 4 * nb;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              pp[(size_t)c * nb + bin] = e ? acc2[p][NC - 4 + c].y : acc2[p][NC - 4 + c].x;
+          }
         }
       }
   }
@@ -573,7 +640,7 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
   return true;
 }
 
-template <int THREADS, int W, int MINB, bool TC>
+template <int THREADS, int W, int MINB, bool TC, bool LIT>
 __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
@@ -600,33 +667,33 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     const int chunk = (int)(local / J.n_tiles);
     bool ok;
     if constexpr (TC) ok = process_item_tc<THREADS>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
-    else ok = process_item_fma<THREADS, W, 2>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
+    else ok = process_item_fma<THREADS, W, 2, LIT>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
     if (!ok) return;
   }
 }
 
-template <int T, int W, int MINB, bool TC>
+template <int T, int W, int MINB, bool TC, bool LIT>
 cudaError_t launch_acc(const LaunchArgs& a, int grid, cudaStream_t s) {
-  const size_t smem = Smem<T, TC>::bytes;
+  const size_t smem = Smem<T, TC, LIT>::bytes;
   static bool attr_set = false;  // the opt-in is per kernel and idempotent
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC>,
+    cudaError_t e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  accumulate_kernel<T, W, MINB, TC><<<grid, T, smem, s>>>(a);
+  accumulate_kernel<T, W, MINB, TC, LIT><<<grid, T, smem, s>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }
 
-template <int T, int W, int MINB, bool TC>
+template <int T, int W, int MINB, bool TC, bool LIT>
 int blocks_per_sm() {
   int nb = 0;
-  const size_t smem = Smem<T, TC>::bytes;
-  cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC>,
+  const size_t smem = Smem<T, TC, LIT>::bytes;
+  cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accumulate_kernel<T, W, MINB, TC>, T,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accumulate_kernel<T, W, MINB, TC, LIT>, T,
                                                     smem) != cudaSuccess ||
       nb < 1)
     nb = 1;
@@ -636,12 +703,14 @@ int blocks_per_sm() {
 }  // namespace
 
 // Variants (rad_impl.h: variant_info): 0 FP32 256x2, 1 FP32 256x4, 2 FP32 128x2,
-// 3 tensor-core 256 (3 CTAs/SM), 4 tensor-core 256 (4 CTAs/SM), 5 FP32 256x2 (4 CTAs/SM).
+// 3 tensor-core 256 (3 CTAs/SM), 4 tensor-core 256 (4 CTAs/SM), 5 FP32 256x2 (4 CTAs/SM),
+// 6 FP32 256x2 with the literal sum (2 CTAs/SM).
 size_t accumulate_smem_bytes(int variant) {
   switch (variant) {
     case 2: return Smem<128, false>::bytes;
     case 3:
     case 4: return Smem<256, true>::bytes;
+    case 6: return Smem<256, false, true>::bytes;
     default: return Smem<256, false>::bytes;
   }
 }
@@ -651,12 +720,13 @@ int accumulate_blocks_per_sm(int variant) {
   if (variant < 0 || variant >= kNumVariants) variant = 0;
   if (cached[variant] == 0) {
     switch (variant) {
-      case 1: cached[1] = blocks_per_sm<256, 4, 2, false>(); break;
-      case 2: cached[2] = blocks_per_sm<128, 2, 6, false>(); break;
-      case 3: cached[3] = blocks_per_sm<256, 1, 3, true>(); break;
-      case 4: cached[4] = blocks_per_sm<256, 1, 4, true>(); break;
-      case 5: cached[5] = blocks_per_sm<256, 2, 4, false>(); break;
-      default: cached[0] = blocks_per_sm<256, 2, 3, false>(); break;
+      case 1: cached[1] = blocks_per_sm<256, 4, 2, false, false>(); break;
+      case 2: cached[2] = blocks_per_sm<128, 2, 6, false, false>(); break;
+      case 3: cached[3] = blocks_per_sm<256, 1, 3, true, false>(); break;
+      case 4: cached[4] = blocks_per_sm<256, 1, 4, true, false>(); break;
+      case 5: cached[5] = blocks_per_sm<256, 2, 4, false, false>(); break;
+      case 6: cached[6] = blocks_per_sm<256, 2, 2, false, true>(); break;
+      default: cached[0] = blocks_per_sm<256, 2, 3, false, false>(); break;
     }
   }
   return cached[variant];
@@ -664,12 +734,13 @@ int accumulate_blocks_per_sm(int variant) {
 
 cudaError_t launch_accumulate(int variant, const LaunchArgs& a, int grid, cudaStream_t s) {
   switch (variant) {
-    case 1: return launch_acc<256, 4, 2, false>(a, grid, s);
-    case 2: return launch_acc<128, 2, 6, false>(a, grid, s);
-    case 3: return launch_acc<256, 1, 3, true>(a, grid, s);
-    case 4: return launch_acc<256, 1, 4, true>(a, grid, s);
-    case 5: return launch_acc<256, 2, 4, false>(a, grid, s);
-    default: return launch_acc<256, 2, 3, false>(a, grid, s);
+    case 1: return launch_acc<256, 4, 2, false, false>(a, grid, s);
+    case 2: return launch_acc<128, 2, 6, false, false>(a, grid, s);
+    case 3: return launch_acc<256, 1, 3, true, false>(a, grid, s);
+    case 4: return launch_acc<256, 1, 4, true, false>(a, grid, s);
+    case 5: return launch_acc<256, 2, 4, false, false>(a, grid, s);
+    case 6: return launch_acc<256, 2, 2, false, true>(a, grid, s);
+    default: return launch_acc<256, 2, 3, false, false>(a, grid, s);
   }
 }
 

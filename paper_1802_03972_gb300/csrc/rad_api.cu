@@ -157,10 +157,35 @@ rad_status ensure_capacity(rad_ctx* c, long long n, int n_chunks) {
       c->h_js.chunk_cap = 0;
       return s;
     }
+    if (c->h_js.literal) {
+      if (c->h_js.partials_p) cudaFree(c->h_js.partials_p);
+      s = cuda_check(c, dmalloc(&c->h_js.partials_p, (size_t)cap * 4 * c->n_bins));
+      if (s != RAD_OK) {
+        c->h_js.chunk_cap = 0;
+        return s;
+      }
+    }
     c->h_js.chunk_cap = cap;
     changed = true;
   }
   return changed ? upload_static(c) : RAD_OK;
+}
+
+// Host copy of the amplitude form factor of Table 1 (f(0) = 1), for the
+// per-frequency f^2 table of the literal sum.
+double host_form_factor(int kind, double width, double omega) {
+  const double x = omega * width / (2.0 * 299792458.0);
+  const double s = x == 0.0 ? 1.0 : sin(x) / x;
+  switch (kind) {
+    case RAD_FF_CIC: return s;
+    case RAD_FF_TSC: return s * s;
+    case RAD_FF_QSC: return s * s * s;
+    case RAD_FF_GAUSS: {
+      const double g = omega * width / 299792458.0;
+      return exp(-0.5 * g * g);
+    }
+    default: return 1.0;
+  }
 }
 
 rad_status stage_inputs(rad_ctx* c, long long n, const double*& r, const double*& beta,
@@ -282,8 +307,12 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
   if ((long long)n_omega * n_dir > 0x7fffffffLL) return RAD_EINVAL;
   if (prec != RAD_PREC_MIXED && prec != RAD_PREC_FP64) return RAD_EINVAL;
   if (ff.kind < RAD_FF_POINT || ff.kind > RAD_FF_GAUSS || !(ff.width >= 0.0) ||
-      !isfinite(ff.width) || (ff.flags & ~RAD_FF_3D) != 0)
+      !isfinite(ff.width) || (ff.flags & ~(RAD_FF_3D | RAD_FF_LITERAL)) != 0)
     return RAD_EINVAL;
+  // The literal sum weighs each particle with f(omega) of Table 1 (Eq. 12): it
+  // needs the mixed path and the direction-independent form factor.
+  const bool literal = (ff.flags & RAD_FF_LITERAL) != 0;
+  if (literal && (prec != RAD_PREC_MIXED || (ff.flags & RAD_FF_3D))) return RAD_EINVAL;
   for (int i = 0; i < n_omega; ++i)
     if (!(omega[i] > 0.0) || !isfinite(omega[i])) return RAD_EINVAL;
   std::vector<double> nd((size_t)3 * n_dir);
@@ -370,9 +399,13 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
   chk(dmalloc(&c->d_spec, (size_t)3 * c->n_bins));
   if (prec == RAD_PREC_MIXED) {
     chk(dmalloc(&c->d_state, (size_t)2 * kComps * c->n_bins));
-    // Enough arrival counters for any tiling (frequency tiles are >= 64 wide).
-    c->tile_cnt_cap = ((n_omega + 63) / 64) * n_dir + 1;
+    // Enough arrival counters for any tiling (frequency tiles are >= 32 wide).
+    c->tile_cnt_cap = ((n_omega + 31) / 32) * n_dir + 1;
     chk(dmalloc(&c->d_tile_cnt, (size_t)c->tile_cnt_cap));
+    if (literal) {
+      chk(dmalloc(&c->d_state_p, (size_t)8 * c->n_bins));
+      chk(dmalloc(&c->d_f2, (size_t)n_omega));
+    }
   } else {
     chk(dmalloc(&c->d_state64, (size_t)12 * c->n_bins));
   }
@@ -387,6 +420,15 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
     if (prec == RAD_PREC_MIXED) {
       chk(cudaMemset(c->d_state, 0, sizeof(float) * 2 * kComps * c->n_bins));
       chk(cudaMemset(c->d_tile_cnt, 0, sizeof(unsigned) * c->tile_cnt_cap));
+      if (literal && s == RAD_OK) {
+        std::vector<float> f2(n_omega);
+        for (int i = 0; i < n_omega; ++i) {
+          const double f = host_form_factor(ff.kind, ff.width, omega[i]);
+          f2[i] = (float)(f * f);
+        }
+        chk(cudaMemset(c->d_state_p, 0, sizeof(float) * 8 * c->n_bins));
+        chk(cudaMemcpy(c->d_f2, f2.data(), sizeof(float) * n_omega, cudaMemcpyHostToDevice));
+      }
     } else {
       chk(cudaMemset(c->d_state64, 0, sizeof(double) * 12 * c->n_bins));
     }
@@ -400,6 +442,14 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
   js.tile_cnt = c->d_tile_cnt;
   js.ref = c->d_ref;
   js.status = c->d_status;
+  js.literal = literal ? 1 : 0;
+  js.f2_tab = c->d_f2;
+  js.state_p = c->d_state_p;
+  if (literal) {
+    c->tile.variant = kLiteralVariant;
+    c->tile.omega_tile = default_omega_tile(kLiteralVariant, n_omega);
+    fill_tiles(js, c->tile.variant, c->tile.omega_tile);
+  }
   if (s == RAD_OK) chk(cudaMemcpy(c->d_js, &js, sizeof(JobStatic), cudaMemcpyHostToDevice));
   if (s != RAD_OK) {
     rad_destroy(c);
@@ -414,7 +464,8 @@ void rad_destroy(rad_ctx* c) {
   cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->d_omega, c->d_om_turns, c->d_om_tab, c->d_dirs, c->d_dir_tab, c->d_ref,
                   c->d_status, c->d_counter, c->d_js, c->d_spec, c->d_state, c->d_state64,
-                  c->d_tile_cnt, c->h_js.rec, c->h_js.partials, c->d_stage};
+                  c->d_tile_cnt, c->h_js.rec, c->h_js.partials, c->d_stage, c->d_state_p,
+                  c->d_f2, c->h_js.partials_p, c->d_push, c->d_push_bdot};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
@@ -467,8 +518,9 @@ rad_status rad_sync(rad_ctx* c) {
 rad_status rad_spectrum_ff(rad_ctx* c, rad_ff ff, double* coh, double* inc, double* tot) {
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  // RAD_FF_LITERAL only matters at creation; the readout ignores it.
   if (ff.kind < RAD_FF_POINT || ff.kind > RAD_FF_GAUSS || !(ff.width >= 0.0) ||
-      !isfinite(ff.width) || (ff.flags & ~RAD_FF_3D) != 0)
+      !isfinite(ff.width) || (ff.flags & ~(RAD_FF_3D | RAD_FF_LITERAL)) != 0)
     return fail(c, RAD_EINVAL);
   double* outs[3] = {coh, inc, tot};
   double* dev_out[3];
@@ -503,9 +555,29 @@ rad_status rad_reset(rad_ctx* c) {
                       : cudaMemsetAsync(c->d_state64, 0, sizeof(double) * 12 * c->n_bins, c->stream);
   rad_status s = cuda_check(c, e);
   if (s != RAD_OK) return s;
+  if (c->d_state_p) {
+    s = cuda_check(c, cudaMemsetAsync(c->d_state_p, 0, sizeof(float) * 8 * c->n_bins, c->stream));
+    if (s != RAD_OK) return s;
+  }
   s = cuda_check(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
   if (s == RAD_OK) c->last_err = RAD_OK;
   return s;
+}
+
+rad_status rad_spectrum_literal(rad_ctx* c, double* out) {
+  if (!c || !out) return RAD_EINVAL;
+  if (c->failed) return RAD_ESTATE;
+  if (!c->d_state_p) return fail(c, RAD_ESTATE);
+  const bool host = !is_device_ptr(out);
+  double* dst = host ? c->d_spec : out;
+  rad_status s = cuda_check(c, launch_readout_literal(c->d_state_p, c->n_bins, dst, c->stream));
+  if (s != RAD_OK) return s;
+  if (host) {
+    s = cuda_check(c, cudaMemcpyAsync(out, dst, sizeof(double) * c->n_bins, cudaMemcpyDeviceToHost,
+                                      c->stream));
+    if (s != RAD_OK) return s;
+  }
+  return check_status_word(c);
 }
 
 rad_status rad_last_error(const rad_ctx* c) { return c ? c->last_err : RAD_EINVAL; }
@@ -537,7 +609,12 @@ rad_status rad_profile_read(rad_ctx* c, double* prepass_ms, double* accumulate_m
   return RAD_OK;
 }
 
+// Mixed: the 16 accumulator floats per bin, then (literal mode) the 8 of P.
 static size_t payload_bytes(const rad_ctx* c) {
+  if (c->prec != RAD_PREC_MIXED) return sizeof(double) * 12 * (size_t)c->n_bins;
+  return sizeof(float) * (2 * kComps + (c->d_state_p ? 8 : 0)) * (size_t)c->n_bins;
+}
+static size_t main_payload_bytes(const rad_ctx* c) {
   return c->prec == RAD_PREC_MIXED ? sizeof(float) * 2 * kComps * (size_t)c->n_bins
                                    : sizeof(double) * 12 * (size_t)c->n_bins;
 }
@@ -558,14 +635,20 @@ rad_status rad_state_export(rad_ctx* c, void* buf, size_t n) {
   h.prec = c->prec;
   h.n_omega = c->n_omega;
   h.n_dir = c->n_dir;
-  h.n_comp = c->prec == RAD_PREC_MIXED ? 2 * kComps : 12;
+  h.n_comp = c->prec == RAD_PREC_MIXED ? 2 * kComps + (c->d_state_p ? 8 : 0) : 12;
   h.elem_size = c->prec == RAD_PREC_MIXED ? 4 : 8;
   h.payload_bytes = payload_bytes(c);
   memcpy(buf, &h, sizeof(h));
   const void* src = c->prec == RAD_PREC_MIXED ? (const void*)c->d_state : (const void*)c->d_state64;
-  rad_status s = cuda_check(c, cudaMemcpyAsync((char*)buf + sizeof(h), src, h.payload_bytes,
+  rad_status s = cuda_check(c, cudaMemcpyAsync((char*)buf + sizeof(h), src, main_payload_bytes(c),
                                                cudaMemcpyDeviceToHost, c->stream));
   if (s != RAD_OK) return s;
+  if (c->d_state_p) {
+    s = cuda_check(c, cudaMemcpyAsync((char*)buf + sizeof(h) + main_payload_bytes(c), c->d_state_p,
+                                      sizeof(float) * 8 * c->n_bins, cudaMemcpyDeviceToHost,
+                                      c->stream));
+    if (s != RAD_OK) return s;
+  }
   return cuda_check(c, cudaStreamSynchronize(c->stream));
 }
 
@@ -587,8 +670,16 @@ rad_status rad_state_import(rad_ctx* c, const void* buf, size_t n) {
   if (check_blob(c, buf, n) != RAD_OK) return fail(c, RAD_EINVAL);
   void* dst = c->prec == RAD_PREC_MIXED ? (void*)c->d_state : (void*)c->d_state64;
   rad_status s = cuda_check(c, cudaMemcpyAsync(dst, (const char*)buf + sizeof(BlobHeader),
-                                               payload_bytes(c), cudaMemcpyHostToDevice, c->stream));
+                                               main_payload_bytes(c), cudaMemcpyHostToDevice,
+                                               c->stream));
   if (s != RAD_OK) return s;
+  if (c->d_state_p) {
+    s = cuda_check(c, cudaMemcpyAsync(c->d_state_p,
+                                      (const char*)buf + sizeof(BlobHeader) + main_payload_bytes(c),
+                                      sizeof(float) * 8 * c->n_bins, cudaMemcpyHostToDevice,
+                                      c->stream));
+    if (s != RAD_OK) return s;
+  }
   return cuda_check(c, cudaStreamSynchronize(c->stream));
 }
 
@@ -603,8 +694,14 @@ rad_status rad_state_merge(rad_ctx* c, const void* buf, size_t n) {
                                     cudaMemcpyHostToDevice, c->stream));
   if (s == RAD_OK) {
     s = c->prec == RAD_PREC_MIXED
-            ? cuda_check(c, launch_state_add(c->d_state, (const float*)tmp, c->n_bins, c->stream))
+            ? cuda_check(c, launch_state_add(c->d_state, (const float*)tmp, c->n_bins, kComps,
+                                             c->stream))
             : cuda_check(c, launch_state64_add(c->d_state64, (const double*)tmp, c->n_bins, c->stream));
+  }
+  if (s == RAD_OK && c->d_state_p) {
+    s = cuda_check(c, launch_state_add(c->d_state_p,
+                                       (const float*)((const char*)tmp + main_payload_bytes(c)),
+                                       c->n_bins, 4, c->stream));
   }
   if (s == RAD_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream));
   cudaFree(tmp);
@@ -622,6 +719,8 @@ rad_status rad_set_tile(rad_ctx* c, const rad_tile* t) {
   if (c->failed) return RAD_ESTATE;
   if (c->prec != RAD_PREC_MIXED) return fail(c, RAD_EINVAL);
   if (t->variant < 0 || t->variant >= kNumVariants) return fail(c, RAD_EINVAL);
+  // The literal sum has its own kernel variant, used only by literal contexts.
+  if ((t->variant == kLiteralVariant) != (c->h_js.literal != 0)) return fail(c, RAD_EINVAL);
   int wt = t->omega_tile > 0 ? t->omega_tile : default_omega_tile(t->variant, c->n_omega);
   if (!valid_omega_tile(t->variant, wt)) return fail(c, RAD_EINVAL);
   if (t->chunk < 0 || (t->chunk % kChunkAlign) != 0) return fail(c, RAD_EINVAL);

@@ -253,7 +253,8 @@ rad_status rad_batch_create(rad_ctx* const* ctxs, int32_t n_jobs, void* stream, 
   *out = nullptr;
   if (!ctxs || n_jobs < 1) return RAD_EINVAL;
   for (int i = 0; i < n_jobs; ++i) {
-    if (!ctxs[i] || ctxs[i]->prec != RAD_PREC_MIXED || ctxs[i]->failed) return RAD_EINVAL;
+    if (!ctxs[i] || ctxs[i]->prec != RAD_PREC_MIXED || ctxs[i]->failed || ctxs[i]->h_js.literal)
+      return RAD_EINVAL;
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return RAD_EINVAL;
   }

@@ -27,6 +27,15 @@ struct rad_ctx {
   double* d_spec = nullptr;      // [3][n_bins] readout staging for host outputs
   float* d_state = nullptr;      // MIXED: [16][n_bins]
   double* d_state64 = nullptr;   // FP64:  [12][n_bins]
+  // in-situ coupling (rad_push_step): three step slots of r, beta, w and beta_dot
+  double* d_push = nullptr;      // [3][7 n_push] doubles: r (3n), beta (3n), w (n) per slot
+  double* d_push_bdot = nullptr; // [3 n_push]
+  long long n_push = 0;          // particle count of the held steps (0: none)
+  int push_held = 0;             // steps held (0, 1, 2)
+  int push_slot[2] = {0, 1};     // slots of the older / newer held step
+  double push_t[3] = {0, 0, 0}, push_dt[3] = {0, 0, 0};
+  float* d_state_p = nullptr;    // literal mode: [8][n_bins]
+  float* d_f2 = nullptr;         // literal mode: [n_omega] f(omega)^2
   unsigned* d_tile_cnt = nullptr;
   int tile_cnt_cap = 0;
   double* d_stage = nullptr;     // staging for host particle arrays

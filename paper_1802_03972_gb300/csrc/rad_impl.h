@@ -53,6 +53,11 @@ struct JobStatic {
   float* rec;
   double* ref;                    // [4]: reference position xyz, t (per call)
   int* status;
+  // literal mode (RAD_FF_LITERAL): the paper's sum P with weights F_k(omega)
+  int literal;
+  const float* f2_tab;            // [n_omega] f(omega)^2 of the creation shape
+  float* state_p;                 // [8][n_bins]: P.e1, P.e2 re/im sums, then compensations
+  float* partials_p;              // [chunk_cap][4][n_bins]
 };
 
 // Per-call data of one job.
@@ -87,8 +92,10 @@ struct Variant {
 };
 // 0-2, 5: FP32-FMA accumulation, w frequencies per thread;
 // 3-4: tensor-core accumulation, a warp covers 32 frequencies (w = 1 in the
-// tiling rules: bins per tile = threads x w, frequency tiles multiples of 32 w).
-constexpr int kNumVariants = 6;
+// tiling rules: bins per tile = threads x w, frequency tiles multiples of 32 w);
+// 6: FP32-FMA with the paper's literal sum as well (literal contexts only).
+constexpr int kNumVariants = 7;
+constexpr int kLiteralVariant = 6;
 inline Variant variant_info(int v) {
   switch (v) {
     case 1: return {256, 4};
@@ -98,6 +105,7 @@ inline Variant variant_info(int v) {
     default: return {256, 2};
   }
 }
+cudaError_t launch_readout_literal(const float* state_p, int n_bins, double* out, cudaStream_t s);
 
 // Launchers (rad_kernels.cu). All enqueue on `s` and return the launch error.
 cudaError_t launch_prepass(const LaunchArgs& a, int total_blocks, cudaStream_t s);
@@ -111,7 +119,8 @@ cudaError_t launch_fp64(const double* omega, const double* dirs, int n_omega, in
                         long long n, const double* r, const double* beta, const double* bdot,
                         const double* w, double t, double dt, double* state64, int* status,
                         cudaStream_t s);
-cudaError_t launch_state_add(float* state, const float* other, int n_bins, cudaStream_t s);
+cudaError_t launch_state_add(float* state, const float* other, int n_bins, int n_comps,
+                             cudaStream_t s);
 cudaError_t launch_state64_add(double* state, const double* other, int n_bins, cudaStream_t s);
 
 void count_launches(int n);

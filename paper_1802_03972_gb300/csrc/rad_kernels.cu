@@ -31,7 +31,7 @@ constexpr double kPi = 3.14159265358979323846;
 
 // ------------------------------------------------------------------ prepass
 // Record layout (floats): 0-2 (r - r_ref)/c hi, 3-5 lo, 6-8 beta hi, 9-11 beta
-// lo, 12-14 beta_dot, 15 1/gamma^2, 16 w dt, 17 sqrt(w) dt, 18-19 unused.
+// lo, 12-14 beta_dot, 15 1/gamma^2, 16 w dt, 17 sqrt(w) dt, 18 w - 1, 19 unused.
 __global__ void __launch_bounds__(256) prepass_kernel(LaunchArgs a) {
   const int j = dev::find_job_block(a, blockIdx.x);
   const JobStatic& J = a.js[j];
@@ -70,14 +70,14 @@ __global__ void __launch_bounds__(256) prepass_kernel(LaunchArgs a) {
     v[15] = __double2float_rn(g2);
     v[16] = __double2float_rn(w * K.dt);
     v[17] = __double2float_rn(sqrt(w) * K.dt);
+    v[18] = __double2float_rn(w - 1.0);
   } else {
     atomicOr(J.status, ST_BAD_PARTICLE);
 #pragma unroll
-    for (int f = 0; f < 18; ++f) v[f] = 0.0f;
+    for (int f = 0; f < 19; ++f) v[f] = 0.0f;
     v[8] = 0.5f;   // a harmless finite beta (zero weights)
     v[15] = 0.75f;
   }
-  v[18] = 0.0f;
   v[19] = 0.0f;
   float4* dst = reinterpret_cast<float4*>(J.rec + (size_t)k * kRecFields);
 #pragma unroll
@@ -195,16 +195,32 @@ __global__ void __launch_bounds__(128) fp64_kernel(const double* __restrict__ om
   }
 }
 
+// Literal spectrum K0 |P|^2 from the compensated P.e1, P.e2 sums.
+__global__ void readout_literal_kernel(const float* __restrict__ state_p, int n_bins, double k0,
+                                       double* out) {
+  const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bin >= n_bins) return;
+  double p2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double x = (double)state_p[(size_t)c * n_bins + bin] -
+                     (double)state_p[(size_t)(4 + c) * n_bins + bin];
+    p2 += x * x;
+  }
+  out[bin] = k0 * p2;
+}
+
+// Adds another accumulator array into state with compensation.  Both hold
+// n_comps sums followed by their n_comps compensations per bin.
 __global__ void state_add_kernel(float* __restrict__ state, const float* __restrict__ other,
-                                 int n_bins) {
+                                 int n_bins, int n_comps) {
   const int bin = blockIdx.x * blockDim.x + threadIdx.x;
   if (bin >= n_bins) return;
   // other holds (sum, comp) pairs; add its value sum - comp with compensation.
-#pragma unroll
-  for (int c = 0; c < kComps; ++c) {
-    const float x = __fsub_rn(other[(size_t)c * n_bins + bin], other[(size_t)(kComps + c) * n_bins + bin]);
+  for (int c = 0; c < n_comps; ++c) {
+    const float x = __fsub_rn(other[(size_t)c * n_bins + bin], other[(size_t)(n_comps + c) * n_bins + bin]);
     float* sum = &state[(size_t)c * n_bins + bin];
-    float* cmp = &state[(size_t)(kComps + c) * n_bins + bin];
+    float* cmp = &state[(size_t)(n_comps + c) * n_bins + bin];
     const float y = __fsub_rn(x, *cmp);
     const float tt = __fadd_rn(*sum, y);
     *cmp = __fsub_rn(__fsub_rn(tt, *sum), y);
@@ -254,8 +270,16 @@ cudaError_t launch_fp64(const double* omega, const double* dirs, int n_omega, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_state_add(float* state, const float* other, int n_bins, cudaStream_t s) {
-  state_add_kernel<<<(n_bins + 255) / 256, 256, 0, s>>>(state, other, n_bins);
+cudaError_t launch_state_add(float* state, const float* other, int n_bins, int n_comps,
+                             cudaStream_t s) {
+  state_add_kernel<<<(n_bins + 255) / 256, 256, 0, s>>>(state, other, n_bins, n_comps);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_readout_literal(const float* state_p, int n_bins, double* out, cudaStream_t s) {
+  const double k0 = kQe * kQe / (16.0 * kPi * kPi * kPi * kEps0 * kC);
+  readout_literal_kernel<<<(n_bins + 255) / 256, 256, 0, s>>>(state_p, n_bins, k0, out);
   count_launches(1);
   return cudaGetLastError();
 }

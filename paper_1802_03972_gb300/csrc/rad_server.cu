@@ -300,6 +300,7 @@ rad_status rad_job_submit(rad_server* s, const rad_job_desc* d, rad_job_id* id) 
   if (d->n_omega < 1 || d->n_dir < 1 || d->max_particles < 1 || d->max_queued < 1)
     return RAD_EINVAL;
   if ((long long)d->n_omega * d->n_dir > 0x7fffffffLL) return RAD_EINVAL;
+  if (d->ff.flags & RAD_FF_LITERAL) return RAD_EINVAL;  // literal contexts run on their own
   auto j = std::make_unique<Job>();
   j->omega.assign(d->omega, d->omega + d->n_omega);
   j->dirs.assign(d->dirs, d->dirs + 3 * (size_t)d->n_dir);

@@ -95,6 +95,7 @@ extern "C" rad_status rad_tune(rad_ctx* c, int64_t n) {
   if (!c || n < 1) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
   if (c->prec != RAD_PREC_MIXED) return RAD_OK;  // the FP64 kernel has no tiles
+  if (c->h_js.literal) return RAD_OK;             // the literal sum has one variant
   const Key key(c->n_omega, c->n_dir, bucket(n));
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -106,6 +107,7 @@ extern "C" rad_status rad_tune(rad_ctx* c, int64_t n) {
   // automatic chunking and half / double of it.
   std::vector<rad_tile> cands;
   for (int v = 0; v < kNumVariants; ++v) {
+    if (v == kLiteralVariant) continue;
     const int wt0 = default_omega_tile(v, c->n_omega);
     for (int wt : {wt0 / 2, wt0, wt0 * 2}) {
       if (!valid_omega_tile(v, wt)) continue;

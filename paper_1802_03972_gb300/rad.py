@@ -32,7 +32,9 @@ EXPORTS = [
     "rad_job_finish", "rad_job_poll", "rad_job_result", "rad_server_stats_get",
     "rad_server_destroy", "rad_status_str", "rad_last_error", "rad_kernel_launch_count",
     "rad_probe_peaks", "rad_profile_enable", "rad_profile_read", "rad_accumulate_static",
+    "rad_spectrum_literal", "rad_push_step", "rad_push_flush",
 ]
+FF_LITERAL = 2  # rad_ff.flags at creation: also accumulate the paper's literal sum
 
 # Limits of rad_accumulate_static (include/rad.h).
 STATIC_MAX_OMEGA, STATIC_MAX_DIRS, STATIC_MAX_BINS, STATIC_MAX_PARTICLES = 4096, 4096, 65536, 65536
@@ -120,6 +122,9 @@ def load(path: str = LIB_PATH):
         "rad_profile_enable": (st, [vp, i32]),
         "rad_profile_read": (st, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(i64)]),
         "rad_accumulate_static": (st, [vp, i32, vp, i32, i64, vp, vp, vp, vp, dbl, dbl, vp, vp]),
+        "rad_spectrum_literal": (st, [vp, vp]),
+        "rad_push_step": (st, [vp, i64, vp, vp, vp, dbl, dbl]),
+        "rad_push_flush": (st, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -239,6 +244,24 @@ class Context:
             flags = int(ff[2]) if len(ff) > 2 else 0
             st = self._lib.rad_spectrum_ff(self._h, rad_ff(int(ff[0]), flags, float(ff[1])), *ptrs)
         _check(st, "rad_spectrum")
+        return out
+
+    def push_step(self, r, beta, w, t: float, dt: float) -> None:
+        """In-situ coupling: hand over one step without beta_dot (finite differences
+        of consecutive steps on the device; see rad_push_step)."""
+        n = int(w.shape[0])
+        _check_particles(n, r, beta, w)
+        _check(self._lib.rad_push_step(self._h, n, _ptr(r), _ptr(beta), _ptr(w), float(t), float(dt)),
+               "rad_push_step")
+
+    def push_flush(self) -> None:
+        _check(self._lib.rad_push_flush(self._h), "rad_push_flush")
+
+    def spectrum_literal(self, out=None):
+        """The paper's literal spectrum K0 |P|^2 (contexts created with FF_LITERAL)."""
+        if out is None:
+            out = np.zeros((self.n_dir, self.n_omega))
+        _check(self._lib.rad_spectrum_literal(self._h, _ptr(out)), "rad_spectrum_literal")
         return out
 
     def sync(self) -> None:
