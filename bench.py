@@ -133,12 +133,14 @@ def traffic_per_launch(updates_per_step: int, tile):
     """DRAM bytes per accumulate launch from the committed ncu summary, scaled to this
     launch's updates; None when the kernel source or the tile changed since the capture."""
     try:
-        t = json.load(open(TRAFFIC_FILE))
-    except (OSError, ValueError):
+        captures = json.load(open(TRAFFIC_FILE))["captures"]
+    except (OSError, ValueError, KeyError):
         return None
-    if t.get("kernel_sha") != kernel_hash() or list(t.get("tile", [])) != list(tile):
-        return None
-    return t["dram_bytes_per_launch"] * updates_per_step / t["updates_per_launch"]
+    sha = kernel_hash()
+    for t in captures:
+        if t.get("kernel_sha") == sha and list(t.get("tile", [])) == list(tile):
+            return t["dram_bytes_per_launch"] * updates_per_step / t["updates_per_launch"]
+    return None
 
 
 def cpu_oracle_rate(wl, n_bins: int, target_s: float):
