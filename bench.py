@@ -40,7 +40,9 @@ VARIANT_NAMES = {0: "FP32 FMA, 256 threads x 2 omega, 3 CTAs/SM",
                  2: "FP32 FMA, 128 threads x 2 omega, 6 CTAs/SM",
                  3: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads, 3 CTAs/SM",
                  4: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads, 4 CTAs/SM",
-                 5: "FP32 FMA, 256 threads x 2 omega, 4 CTAs/SM"}
+                 5: "FP32 FMA, 256 threads x 2 omega, 4 CTAs/SM",
+                 7: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads, 3 CTAs/SM, "
+                    "two frequency passes per staged particle tile"}
 KERNEL_SRC = os.path.join(ROOT, "paper_1802_03972_gb300", "csrc", "rad_accumulate.cu")
 
 
@@ -258,10 +260,26 @@ def batch_leg(rounds: int, n_jobs: int = 64):
             "graph_replay": True}
 
 
-def serve_leg(n_jobs: int, load: float, rate: float | None, steps_range=(5, 20), seed: int = 5):
+def fifo_latencies(arrivals, work, rate: float):
+    """Arrival-to-result latencies of one-job-at-a-time FIFO service at `rate` updates/s."""
+    import numpy as np
+    free, lat = 0.0, []
+    for a, u in zip(arrivals, work):
+        free = max(free, a) + u / rate
+        lat.append(free - a)
+    lat = np.array(lat)
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "rate": rate}
+
+
+def serve_leg(n_jobs: int, load: float, rate: float | None, steps_range=(5, 20), seed: int = 5,
+              cap: float = 1.6e12, fifo_rates=None):
     """Continuous batching: Poisson arrivals of the batched job mix (steps per job
     scaled to steps_range), each job fed step by step from device buffers; p50/p99
-    of arrival-to-result latency and the throughput of the window."""
+    of arrival-to-result latency and the throughput of the window.  `cap` is the
+    measured single-GPU rate the load is relative to; `fifo_rates` names measured
+    single-job rates whose one-job-at-a-time FIFO latencies over the same arrivals
+    are reported beside (computed from those rates, not run)."""
     import numpy as np
     import torch
 
@@ -273,7 +291,6 @@ def serve_leg(n_jobs: int, load: float, rate: float | None, steps_range=(5, 20),
     for wl in wls:
         st = wl.step(0)
         dev.append([torch.from_numpy(a).cuda() for a in (st.r, st.beta, st.beta_dot, st.w)])
-    cap = 1.6e12  # updates/s of one GB300 on this kernel (bench headline)
     lam = rate if rate else load * cap / float(np.mean(work))
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / lam, n_jobs))
@@ -312,11 +329,15 @@ def serve_leg(n_jobs: int, load: float, rate: float | None, steps_range=(5, 20),
     stats = srv.stats()
     srv.close()
     lat = np.array(lat)
-    return {"jobs": n_jobs, "arrival_rate_per_s": lam, "load": load if not rate else None,
-            "steps_per_job": list(steps_range), "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
-            "value": float(sum(work)) / makespan, "unit": UNIT, "makespan_s": makespan,
-            "rounds": stats["rounds"], "peak_footprint_bytes": stats["peak_footprint_bytes"]}
+    out = {"jobs": n_jobs, "arrival_rate_per_s": lam, "load": load if not rate else None,
+           "steps_per_job": list(steps_range), "p50_s": float(np.percentile(lat, 50)),
+           "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+           "value": float(sum(work)) / makespan, "unit": UNIT, "makespan_s": makespan,
+           "rounds": stats["rounds"], "peak_footprint_bytes": stats["peak_footprint_bytes"]}
+    if fifo_rates:
+        out["fifo_one_job_at_a_time"] = {k: fifo_latencies(arrivals, work, r)
+                                         for k, r in fifo_rates.items() if r}
+    return out
 
 
 def main():
@@ -383,6 +404,7 @@ def main():
     clocks = clk.stop()
     launches = rad.kernel_launch_count() - launches0
     pre_ms, acc_ms, calls = ctx.profile_read()
+    eff_mhz = ctx.profile_clock()
     ctx.profile(False)
     if dist:
         t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
@@ -429,6 +451,11 @@ def main():
             "accumulate_ms_per_step": acc_ms / max(calls, 1)}
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
+    if eff_mhz > 0:
+        # the SM clock the accumulate kernel actually ran at (its CTAs' cycle
+        # counters over elapsed time), and the fraction of the peak at that clock
+        roof["sm_mhz_in_kernel"] = eff_mhz
+        roof["frac_at_kernel_clock"] = achieved / (peak * eff_mhz / SM_MAX_MHZ)
 
     # End to end through the C ABI with pinned host buffers: H2D of each step's
     # particles inside rad_accumulate, D2H of the spectra by rad_spectrum.
@@ -489,15 +516,24 @@ def main():
         batched = batch_leg(args.batch_rounds)
     served = served_literal = None
     if not args.no_serve and rank == 0:
-        served = serve_leg(args.serve_jobs, args.serve_load, args.serve_rate)
-        # the literal arrival rate of the serving workload: 200 jobs/s, a window of 32
-        served_literal = serve_leg(32, args.serve_load, 200.0, seed=6)
+        single = batched["unbatched_value"] if batched else value / world
+        fifo = {"mixed_single_job": single, "fp64_plain": fp64["value"] if fp64 else None}
+        served = serve_leg(args.serve_jobs, args.serve_load, args.serve_rate, cap=value / world,
+                           fifo_rates=fifo)
+        # the literal arrival rate of the serving workload: 200 jobs/s over a window of
+        # 256 arrivals (steps per job scaled further so the backlog drains in seconds)
+        served_literal = serve_leg(256, args.serve_load, 200.0, steps_range=(2, 8), seed=6,
+                                   cap=value / world, fifo_rates=fifo)
 
     peaks = None
     if args.peaks and rank == 0:
         p = rad.probe_peaks()
         peaks = {"ffma_lanes_per_clk_sm": p[0], "ffma2_lanes_per_clk_sm": p[2],
                  "mufu_per_clk_sm": p[4], "dfma_per_clk_sm": p[6], "probe_mhz": p[5]}
+        q = rad.probe_tensor()
+        peaks["tensor"] = {"mma_sync_tf32_mac_per_clk_sm": q[0],
+                           "tcgen05_tf32_clk_per_mma_n16_64_128_256": list(q[1:5]),
+                           "tcgen05_f16_clk_per_mma_n16_256": list(q[5:7]), "probe_mhz": q[7]}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

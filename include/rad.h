@@ -296,6 +296,13 @@ rad_status rad_profile_enable(rad_ctx* ctx, int32_t on);
 rad_status rad_profile_read(rad_ctx* ctx, double* prepass_ms, double* accumulate_ms,
                             int64_t* calls);
 
+/* Effective SM clock of the accumulate kernels timed since the last call (or
+ * since profiling was enabled): the SM cycle counter divided by elapsed
+ * nanoseconds, each summed over the kernels' CTA lifetimes, in MHz; 0 when none
+ * ran.  sm_mhz: host double (out).  Synchronises the context's stream and
+ * resets the sums.  RAD_EINVAL for a NULL argument. */
+rad_status rad_profile_clock(rad_ctx* ctx, double* sm_mhz);
+
 /* Accumulation without any allocation.
  *
  * Some callers cannot allocate device memory: code running inside a host

@@ -174,6 +174,113 @@ __global__ void __launch_bounds__(kThreads) k_mix(float* out, long long* cyc, in
   stamp(cyc, t0);
 }
 
+
+// ---- tensor pipes: legacy mma.sync and tcgen05.mma with A in tensor memory ----
+
+constexpr unsigned long long kProbeWaitNs = 1000000000ULL;  // 1 s bound on any wait
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void __launch_bounds__(256) k_mma_sync(float* out, long long* cyc, int iters) {
+  long long t0 = clock64();
+  float d[4][4] = {};
+  const uint32_t a = __float_as_uint(1.0001f + threadIdx.x), b = __float_as_uint(0.999f);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      asm volatile(
+          "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+          "{%0,%1,%2,%3};"
+          : "+f"(d[j][0]), "+f"(d[j][1]), "+f"(d[j][2]), "+f"(d[j][3])
+          : "r"(a), "r"(a), "r"(a), "r"(a), "r"(b), "r"(b));
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) s += d[j][0] + d[j][1] + d[j][2] + d[j][3];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cyc[2 * blockIdx.x] = t0;
+    cyc[2 * blockIdx.x + 1] = clock64();
+  }
+}
+
+// Instruction descriptor of tcgen05.mma, dense, FP32 accumulator, K-major A and
+// B: bits 4-5 D type (1 = F32), 7-9 / 10-12 A / B type (kind::f16: 0 = F16;
+// kind::tf32: 2 = TF32), 17-22 N >> 3, 24-28 M >> 4.
+__host__ __device__ constexpr uint32_t umma_idesc(bool tf32, int m, int n) {
+  return (1u << 4) | ((tf32 ? 2u : 0u) << 7) | ((tf32 ? 2u : 0u) << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+// One CTA of one warp per SM holds all 512 TMEM columns; lane 0 issues `n_mma`
+// MMAs (M = 128, A from TMEM columns 0-63, D in columns 64.., B one 128-byte
+// core matrix in shared memory read with zero strides) and times issue to
+// completion with the SM cycle counter.
+template <int N, bool TF32>
+__global__ void __launch_bounds__(32, 1) k_umma(int n_mma, long long* cyc, int* err) {
+  __shared__ __align__(128) float bcore[64];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t tbase;
+  const int lane = threadIdx.x;
+  for (int i = lane; i < 64; i += 32) bcore[i] = 1e-3f * (float)i;
+  if (lane == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&done)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(&tbase)) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tb = tbase;
+  if (lane == 0) {
+    const uint64_t bdesc = (uint64_t)((su32(bcore) >> 4) & 0x3FFFu) | (1ull << 46);
+    constexpr uint32_t id = umma_idesc(TF32, 128, N);
+    const long long c0 = clock64();
+    for (int i = 0; i < n_mma; ++i) {
+      const uint32_t d = tb + 64u, a = tb + (uint32_t)((i & 7) * 8);
+      if constexpr (TF32)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+            "r"(a), "l"(bdesc), "r"(id), "r"(i > 0 ? 1 : 0)
+            : "memory");
+      else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+            "r"(a), "l"(bdesc), "r"(id), "r"(i > 0 ? 1 : 0)
+            : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&done))
+                 : "memory");
+    const unsigned long long t0 = globaltimer_ns();
+    bool ok = false;
+    while (!ok && globaltimer_ns() - t0 < kProbeWaitNs) {
+      uint32_t r;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(r) : "r"(su32(&done)) : "memory");
+      ok = r != 0;
+    }
+    if (!ok) atomicOr(err, 1);
+    cyc[2 * blockIdx.x] = c0;
+    cyc[2 * blockIdx.x + 1] = clock64();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tb) : "memory");
+}
+
 }  // namespace
 
 extern "C" {
@@ -244,6 +351,74 @@ int rad_probe_peaks(double* out, int n_out) {
   delete[] h_cyc;
   cudaFree(d_out);
   cudaFree(d_cyc);
+  return (int)e;
+}
+
+
+// Tensor pipes: out[0] legacy mma.sync m16n8k8 TF32 MACs / clk / SM; then SM
+// cycles per tcgen05.mma (M = 128, A in tensor memory) for kind::tf32 at
+// N = 16, 64, 128, 256 (out[1..4]) and kind::f16 at N = 16, 256 (out[5], out[6]);
+// out[7] the effective clock (MHz) of the mma.sync probe.
+int rad_probe_tensor(double* out, int n_out) {
+  if (out == nullptr || n_out < 8) return (int)cudaErrorInvalidValue;
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = 4, blocks = n_sm * per_sm;
+  float* d_out = nullptr;
+  long long* d_cyc = nullptr;
+  int* d_err = nullptr;
+  cudaError_t e = cudaMalloc(&d_out, sizeof(float) * blocks * 256);
+  if (e == cudaSuccess) e = cudaMalloc(&d_cyc, sizeof(long long) * 2 * blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(int));
+  long long* h_cyc = new long long[2 * blocks];
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  if (e == cudaSuccess) {
+    const int iters = 4096;
+    k_mma_sync<<<blocks, 256>>>(d_out, d_cyc, 16);
+    cudaEventRecord(ev0);
+    k_mma_sync<<<blocks, 256>>>(d_out, d_cyc, iters);
+    cudaEventRecord(ev1);
+    cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaMemcpy(h_cyc, d_cyc, sizeof(long long) * 2 * blocks, cudaMemcpyDeviceToHost);
+    double cyc_sum = 0.0;
+    for (int b = 0; b < blocks; ++b) cyc_sum += (double)(h_cyc[2 * b + 1] - h_cyc[2 * b]);
+    const double cyc_mean = cyc_sum / blocks;
+    const double macs_per_sm = (double)per_sm * 8 * iters * 4 * 16 * 8 * 8;
+    out[0] = macs_per_sm / cyc_mean;
+    out[7] = cyc_mean / (ms * 1e-3) / 1e6;
+  }
+  auto umma = [&](auto kern, double* res) {
+    if (e != cudaSuccess) return;
+    const int n_mma = 4096;
+    kern<<<n_sm, 32>>>(64, d_cyc, d_err);
+    kern<<<n_sm, 32>>>(n_mma, d_cyc, d_err);
+    e = cudaDeviceSynchronize();
+    int err = 0;
+    cudaMemcpy(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpy(h_cyc, d_cyc, sizeof(long long) * 2 * n_sm, cudaMemcpyDeviceToHost);
+    double cyc_sum = 0.0;
+    for (int b = 0; b < n_sm; ++b) cyc_sum += (double)(h_cyc[2 * b + 1] - h_cyc[2 * b]);
+    *res = err ? -1.0 : cyc_sum / n_sm / n_mma;
+  };
+  umma(k_umma<16, true>, out + 1);
+  umma(k_umma<64, true>, out + 2);
+  umma(k_umma<128, true>, out + 3);
+  umma(k_umma<256, true>, out + 4);
+  umma(k_umma<16, false>, out + 5);
+  umma(k_umma<256, false>, out + 6);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  delete[] h_cyc;
+  cudaFree(d_out);
+  cudaFree(d_cyc);
+  cudaFree(d_err);
   return (int)e;
 }
 

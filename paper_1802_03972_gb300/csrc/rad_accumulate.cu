@@ -119,11 +119,11 @@ __device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
 // Tensor-core variants also keep their per-chunk (second-level) sums in
 // shared memory: 16 floats per thread, one slot per thread and value.
 // The literal variant adds a fourth float4 per record: (w - 1) duplicated.
-template <int THREADS, bool TC, bool LIT = false>
+template <int THREADS, bool TC, bool LIT = false, int PASSES = 1>
 struct Smem {
   static constexpr size_t raw_bytes = (size_t)THREADS * kRecFields * sizeof(float);
   static constexpr size_t rec_bytes = (size_t)THREADS * (TC ? 40 : (LIT ? 64 : 48));
-  static constexpr size_t l2_bytes = TC ? (size_t)THREADS * 16 * sizeof(float) : 0;
+  static constexpr size_t l2_bytes = TC ? (size_t)THREADS * 16 * sizeof(float) * PASSES : 0;
   static constexpr size_t bytes = raw_bytes + 2 * rec_bytes + l2_bytes;
 };
 
@@ -490,45 +490,50 @@ __device__ __forceinline__ void tc_block(float2 pA, float2 pB, uint32_t b0, uint
 
 // Warp layout: warp w handles direction d0 + w / (WT/32) and 32 frequencies
 // (two 16-row MMA blocks) starting at o0 + 32 (w % (WT/32)).
-template <int THREADS>
+template <int THREADS, int PASSES>
 __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCall& K, int tile,
                                                 int chunk, unsigned char* __restrict__ smem,
                                                 uint64_t* bar, uint32_t& phase, int* s_flag) {
   constexpr int NB = 2;  // 16-frequency blocks per warp
-  using S = Smem<THREADS, true>;
+  using S = Smem<THREADS, true, false, PASSES>;
   float* raw = reinterpret_cast<float*>(smem);
   const TileGeom g = tile_geom(J, tile, THREADS);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = lane >> 2, c = lane & 3;
-  const int warps_per_dir = g.WT / (16 * NB);
+  // The tile's frequencies are swept in PASSES passes of PW over the same
+  // staged particle records (one stage 1 and one barrier per tile and pass set).
+  const int PW = g.WT / PASSES;
+  const int warps_per_dir = PW / (16 * NB);
   const int my_dl = warp / warps_per_dir;
   const int my_d_raw = g.d0 + my_dl;
   const int my_d = min(my_d_raw, J.n_dir - 1);
-  const int o_warp = g.o0 + (warp - my_dl * warps_per_dir) * 16 * NB;
+  const int o_warp0 = g.o0 + (warp - my_dl * warps_per_dir) * 16 * NB;
   const int n_om = J.n_omega;
   const int s1_dl = threadIdx.x / g.KT, s1_kk = threadIdx.x - s1_dl * g.KT;
   const int s1_d = min(g.d0 + s1_dl, J.n_dir - 1);
 
   float2 omh[NB], nomh[NB], wh[NB], wl[NB];
+  auto load_omega = [&](int o_warp) {
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int i0 = min(o_warp + 16 * b + r, n_om - 1), i1 = min(o_warp + 16 * b + r + 8, n_om - 1);
-    omh[b] = make_float2(__ldg(J.om_tab + i0), __ldg(J.om_tab + i1));
-    nomh[b] = make_float2(__ldg(J.om_tab + n_om + i0), __ldg(J.om_tab + n_om + i1));
-    wh[b] = make_float2(__ldg(J.om_tab + 2 * n_om + i0), __ldg(J.om_tab + 2 * n_om + i1));
-    wl[b] = make_float2(__ldg(J.om_tab + 3 * n_om + i0), __ldg(J.om_tab + 3 * n_om + i1));
-  }
+    for (int b = 0; b < NB; ++b) {
+      const int i0 = min(o_warp + 16 * b + r, n_om - 1), i1 = min(o_warp + 16 * b + r + 8, n_om - 1);
+      omh[b] = make_float2(__ldg(J.om_tab + i0), __ldg(J.om_tab + i1));
+      nomh[b] = make_float2(__ldg(J.om_tab + n_om + i0), __ldg(J.om_tab + n_om + i1));
+      wh[b] = make_float2(__ldg(J.om_tab + 2 * n_om + i0), __ldg(J.om_tab + 2 * n_om + i1));
+      wl[b] = make_float2(__ldg(J.om_tab + 3 * n_om + i0), __ldg(J.om_tab + 3 * n_om + i1));
+    }
+  };
+  load_omega(o_warp0);
   float dre[NB][4], dim[NB][4];
-  // second-level sums: slot v of this thread at l2[v * THREADS + threadIdx.x]
-  float* l2 = reinterpret_cast<float*>(smem + S::raw_bytes + 2 * S::rec_bytes);
+  // second-level sums of pass p: group q (q = b for the real parts of block b,
+  // NB + b for the imaginary parts) of this thread at l2[(p * 4 + q) * THREADS + threadIdx.x]
+  float4* l2 = reinterpret_cast<float4*>(smem + S::raw_bytes + 2 * S::rec_bytes);
 #pragma unroll
   for (int b = 0; b < NB; ++b)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      dre[b][e] = dim[b][e] = 0.0f;
-      l2[(b * 4 + e) * THREADS + threadIdx.x] = 0.0f;
-      l2[(NB * 4 + b * 4 + e) * THREADS + threadIdx.x] = 0.0f;
-    }
+    for (int e = 0; e < 4; ++e) dre[b][e] = dim[b][e] = 0.0f;
+#pragma unroll
+  for (int v = 0; v < 4 * PASSES; ++v) l2[v * THREADS + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   const long long k_begin = (long long)chunk * K.ck;
   const long long k_end = min(k_begin + (long long)K.ck, K.n);
@@ -570,49 +575,59 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
     const float2* tw = tau2 + my_dl * g.KT;
     const float* aw = ampb + (size_t)my_dl * g.KT * 8;
     const int kn8 = (kn + 7) & ~7;
-    if (!(flags & 1)) {
+#pragma unroll 1
+    for (int ps = 0; ps < PASSES; ++ps) {
+      const int o_warp = o_warp0 + ps * PW;
+      if (PASSES > 1) load_omega(o_warp);
+      if (!(flags & 1)) {
 #pragma unroll 2
-      for (int kk = 0; kk < kn8; kk += 8) {
-        const float2 tA = tw[kk + c], tB = tw[kk + c + 4];
-        const uint32_t b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
-        const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
-        const float2 thA = make_float2(tA.x, tA.x), tlA = make_float2(tA.y, tA.y);
-        const float2 thB = make_float2(tB.x, tB.x), tlB = make_float2(tB.y, tB.y);
+        for (int kk = 0; kk < kn8; kk += 8) {
+          const float2 tA = tw[kk + c], tB = tw[kk + c + 4];
+          const uint32_t b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
+          const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
+          const float2 thA = make_float2(tA.x, tA.x), tlA = make_float2(tA.y, tA.y);
+          const float2 thB = make_float2(tB.x, tB.x), tlB = make_float2(tB.y, tB.y);
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const float2 pA = phase2(omh[b], nomh[b], wh[b], wl[b], thA, tlA);
+            const float2 pB = phase2(omh[b], nomh[b], wh[b], wl[b], thB, tlB);
+            tc_block(pA, pB, b0, b1, dre[b], dim[b]);
+          }
+        }
+      } else {
+        if (threadIdx.x == 0) atomicOr(J.status, ST_SLOW_PHASE);
+        double omt[NB][2];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          const float2 pA = phase2(omh[b], nomh[b], wh[b], wl[b], thA, tlA);
-          const float2 pB = phase2(omh[b], nomh[b], wh[b], wl[b], thB, tlB);
-          tc_block(pA, pB, b0, b1, dre[b], dim[b]);
+          omt[b][0] = J.om_turns[min(o_warp + 16 * b + r, n_om - 1)];
+          omt[b][1] = J.om_turns[min(o_warp + 16 * b + r + 8, n_om - 1)];
+        }
+        for (int kk = 0; kk < kn8; kk += 8) {
+          const float2 tA = tw[kk + c], tB = tw[kk + c + 4];
+          const uint32_t b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
+          const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const float2 pA = make_float2(phase_wide(omt[b][0], tA.x, tA.y), phase_wide(omt[b][1], tA.x, tA.y));
+            const float2 pB = make_float2(phase_wide(omt[b][0], tB.x, tB.y), phase_wide(omt[b][1], tB.x, tB.y));
+            tc_block(pA, pB, b0, b1, dre[b], dim[b]);
+          }
         }
       }
-    } else {
-      if (threadIdx.x == 0) atomicOr(J.status, ST_SLOW_PHASE);
-      double omt[NB][2];
+      float4* l2p = l2 + ps * 4 * THREADS + threadIdx.x;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        omt[b][0] = J.om_turns[min(o_warp + 16 * b + r, n_om - 1)];
-        omt[b][1] = J.om_turns[min(o_warp + 16 * b + r + 8, n_om - 1)];
-      }
-      for (int kk = 0; kk < kn8; kk += 8) {
-        const float2 tA = tw[kk + c], tB = tw[kk + c + 4];
-        const uint32_t b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
-        const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
+        float4 x = l2p[b * THREADS], y = l2p[(NB + b) * THREADS];
+        const float2 x01 = __fadd2_rn(make_float2(x.x, x.y), make_float2(dre[b][0], dre[b][1]));
+        const float2 x23 = __fadd2_rn(make_float2(x.z, x.w), make_float2(dre[b][2], dre[b][3]));
+        const float2 y01 = __fadd2_rn(make_float2(y.x, y.y), make_float2(dim[b][0], dim[b][1]));
+        const float2 y23 = __fadd2_rn(make_float2(y.z, y.w), make_float2(dim[b][2], dim[b][3]));
+        l2p[b * THREADS] = make_float4(x01.x, x01.y, x23.x, x23.y);
+        l2p[(NB + b) * THREADS] = make_float4(y01.x, y01.y, y23.x, y23.y);
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          const float2 pA = make_float2(phase_wide(omt[b][0], tA.x, tA.y), phase_wide(omt[b][1], tA.x, tA.y));
-          const float2 pB = make_float2(phase_wide(omt[b][0], tB.x, tB.y), phase_wide(omt[b][1], tB.x, tB.y));
-          tc_block(pA, pB, b0, b1, dre[b], dim[b]);
-        }
+        for (int e = 0; e < 4; ++e) dre[b][e] = dim[b][e] = 0.0f;
       }
     }
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        l2[(b * 4 + e) * THREADS + threadIdx.x] += dre[b][e];
-        l2[(NB * 4 + b * 4 + e) * THREADS + threadIdx.x] += dim[b][e];
-        dre[b][e] = dim[b][e] = 0.0f;
-      }
   }
 
   // The D fragment holds rows (r, r+8) and columns (2c, 2c+1); columns 0-3 are
@@ -620,15 +635,18 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
   // (c < 2) adds lane c+2's values.
   const int nb = J.n_bins;
   float* part = J.partials + (size_t)chunk * kComps * nb;
+#pragma unroll 1
+  for (int ps = 0; ps < PASSES; ++ps)
 #pragma unroll
   for (int b = 0; b < NB; ++b)
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const float lre = l2[(b * 4 + e) * THREADS + threadIdx.x];
-      const float lim = l2[(NB * 4 + b * 4 + e) * THREADS + threadIdx.x];
+      const float* l2p = reinterpret_cast<const float*>(l2 + ps * 4 * THREADS + threadIdx.x);
+      const float lre = l2p[4 * b * THREADS + e];
+      const float lim = l2p[4 * (NB + b) * THREADS + e];
       const float re = lre + __shfl_xor_sync(0xffffffffu, lre, 2);
       const float im = lim + __shfl_xor_sync(0xffffffffu, lim, 2);
-      const int o = o_warp + 16 * b + r + ((e >> 1) << 3);
+      const int o = o_warp0 + ps * PW + 16 * b + r + ((e >> 1) << 3);
       const int j = 2 * c + (e & 1);  // amplitude column
       if (c < 2 && my_d_raw < J.n_dir && o < n_om) {
         const int bin = my_d * n_om + o;
@@ -640,7 +658,7 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
   return true;
 }
 
-template <int THREADS, int W, int MINB, bool TC, bool LIT>
+template <int THREADS, int W, int MINB, bool TC, bool LIT, int PASSES = 1>
 __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
@@ -651,6 +669,12 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     mbar_fence_init();
   }
   __syncthreads();
+  long long clk0 = 0;
+  unsigned long long ns0 = 0;
+  if (a.prof_clk && threadIdx.x == 0) {
+    clk0 = clock64();
+    ns0 = global_ns();
+  }
   uint32_t phase = 0u;
   int buf = 0;
   for (;;) {
@@ -658,7 +682,7 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     __syncthreads();
     const long long item = s_item[buf];
     buf ^= 1;
-    if (item >= a.n_items) return;
+    if (item >= a.n_items) break;
     const int j = find_job(a, item);
     const JobStatic& J = a.js[j];
     const JobCall K = a.use_inline ? a.inline_call : a.jc[j];
@@ -666,34 +690,38 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     const int tile = (int)(local % J.n_tiles);
     const int chunk = (int)(local / J.n_tiles);
     bool ok;
-    if constexpr (TC) ok = process_item_tc<THREADS>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
+    if constexpr (TC) ok = process_item_tc<THREADS, PASSES>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
     else ok = process_item_fma<THREADS, W, 2, LIT>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
-    if (!ok) return;
+    if (!ok) break;
+  }
+  if (a.prof_clk && threadIdx.x == 0) {
+    atomicAdd(&a.prof_clk[0], (unsigned long long)(clock64() - clk0));
+    atomicAdd(&a.prof_clk[1], global_ns() - ns0);
   }
 }
 
-template <int T, int W, int MINB, bool TC, bool LIT>
+template <int T, int W, int MINB, bool TC, bool LIT, int P = 1>
 cudaError_t launch_acc(const LaunchArgs& a, int grid, cudaStream_t s) {
-  const size_t smem = Smem<T, TC, LIT>::bytes;
+  const size_t smem = Smem<T, TC, LIT, P>::bytes;
   static bool attr_set = false;  // the opt-in is per kernel and idempotent
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT>,
+    cudaError_t e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  accumulate_kernel<T, W, MINB, TC, LIT><<<grid, T, smem, s>>>(a);
+  accumulate_kernel<T, W, MINB, TC, LIT, P><<<grid, T, smem, s>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }
 
-template <int T, int W, int MINB, bool TC, bool LIT>
+template <int T, int W, int MINB, bool TC, bool LIT, int P = 1>
 int blocks_per_sm() {
   int nb = 0;
-  const size_t smem = Smem<T, TC, LIT>::bytes;
-  cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT>,
+  const size_t smem = Smem<T, TC, LIT, P>::bytes;
+  cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accumulate_kernel<T, W, MINB, TC, LIT>, T,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accumulate_kernel<T, W, MINB, TC, LIT, P>, T,
                                                     smem) != cudaSuccess ||
       nb < 1)
     nb = 1;
@@ -704,13 +732,15 @@ int blocks_per_sm() {
 
 // Variants (rad_impl.h: variant_info): 0 FP32 256x2, 1 FP32 256x4, 2 FP32 128x2,
 // 3 tensor-core 256 (3 CTAs/SM), 4 tensor-core 256 (4 CTAs/SM), 5 FP32 256x2 (4 CTAs/SM),
-// 6 FP32 256x2 with the literal sum (2 CTAs/SM).
+// 6 FP32 256x2 with the literal sum (2 CTAs/SM), 7 tensor-core 256 sweeping each staged
+// particle tile in two frequency passes.
 size_t accumulate_smem_bytes(int variant) {
   switch (variant) {
     case 2: return Smem<128, false>::bytes;
     case 3:
     case 4: return Smem<256, true>::bytes;
     case 6: return Smem<256, false, true>::bytes;
+    case 7: return Smem<256, true, false, 2>::bytes;
     default: return Smem<256, false>::bytes;
   }
 }
@@ -726,6 +756,7 @@ int accumulate_blocks_per_sm(int variant) {
       case 4: cached[4] = blocks_per_sm<256, 1, 4, true, false>(); break;
       case 5: cached[5] = blocks_per_sm<256, 2, 4, false, false>(); break;
       case 6: cached[6] = blocks_per_sm<256, 2, 2, false, true>(); break;
+      case 7: cached[7] = blocks_per_sm<256, 1, 3, true, false, 2>(); break;
       default: cached[0] = blocks_per_sm<256, 2, 3, false, false>(); break;
     }
   }
@@ -740,6 +771,7 @@ cudaError_t launch_accumulate(int variant, const LaunchArgs& a, int grid, cudaSt
     case 4: return launch_acc<256, 1, 4, true, false>(a, grid, s);
     case 5: return launch_acc<256, 2, 4, false, false>(a, grid, s);
     case 6: return launch_acc<256, 2, 2, false, true>(a, grid, s);
+    case 7: return launch_acc<256, 1, 3, true, false, 2>(a, grid, s);
     default: return launch_acc<256, 2, 3, false, false>(a, grid, s);
   }
 }

@@ -75,7 +75,7 @@ rad_status cuda_check(rad_ctx* c, cudaError_t e) {
 // Valid tile widths for a variant: 32 * W * m with m dividing THREADS / 32.
 int default_omega_tile(int variant, int n_omega) {
   const Variant v = variant_info(variant);
-  const int wmin = 32 * v.w, wmax = v.threads * v.w;
+  const int wmin = 32 * v.w * v.passes, wmax = v.threads * v.w * v.passes;
   int wt = wmin;
   while (wt < n_omega && wt < wmax) wt *= 2;
   return wt;
@@ -83,16 +83,17 @@ int default_omega_tile(int variant, int n_omega) {
 
 bool valid_omega_tile(int variant, int wt) {
   const Variant v = variant_info(variant);
-  if (wt < 32 * v.w || wt > v.threads * v.w) return false;
-  if (wt % (32 * v.w)) return false;
-  const int m = wt / (32 * v.w);
+  const int unit = 32 * v.w * v.passes;
+  if (wt < unit || wt > v.threads * v.w * v.passes) return false;
+  if (wt % unit) return false;
+  const int m = wt / unit;
   return (v.threads / 32) % m == 0;
 }
 
 void fill_tiles(JobStatic& js, int variant, int wt) {
   const Variant v = variant_info(variant);
   js.wt = wt;
-  js.nt = v.threads * v.w / wt;
+  js.nt = v.threads * v.w * v.passes / wt;
   js.tiles_om = (js.n_omega + wt - 1) / wt;
   js.tiles_dir = (js.n_dir + js.nt - 1) / js.nt;
   js.n_tiles = js.tiles_om * js.tiles_dir;
@@ -271,6 +272,7 @@ rad_status enqueue_accumulate(rad_ctx* c, long long n, const double* r, const do
     ev = &c->prof_ev[c->prof_used];
     c->prof_used += 3;
     cudaEventRecord(ev[0], c->stream);
+    a.prof_clk = c->d_prof_clk;
   }
   s = cuda_check(c, launch_prepass(a, (int)((n + 255) / 256), c->stream));
   if (s != RAD_OK) return s;
@@ -469,6 +471,7 @@ void rad_destroy(rad_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+  if (c->d_prof_clk) cudaFree(c->d_prof_clk);
   cudaGetLastError();
   delete c;
 }
@@ -584,7 +587,29 @@ rad_status rad_last_error(const rad_ctx* c) { return c ? c->last_err : RAD_EINVA
 
 rad_status rad_profile_enable(rad_ctx* c, int32_t on) {
   if (!c) return RAD_EINVAL;
+  if (c->failed) return RAD_ESTATE;
+  if (on && !c->d_prof_clk) {
+    rad_status s = cuda_check(c, cudaMalloc(&c->d_prof_clk, 2 * sizeof(unsigned long long)));
+    if (s == RAD_OK)
+      s = cuda_check(c, cudaMemsetAsync(c->d_prof_clk, 0, 2 * sizeof(unsigned long long), c->stream));
+    if (s != RAD_OK) return s;
+  }
   c->prof_on = on != 0;
+  return RAD_OK;
+}
+
+rad_status rad_profile_clock(rad_ctx* c, double* sm_mhz) {
+  if (!c || !sm_mhz) return RAD_EINVAL;
+  if (c->failed) return RAD_ESTATE;
+  *sm_mhz = 0.0;
+  if (!c->d_prof_clk) return RAD_OK;
+  unsigned long long h[2] = {0, 0};
+  rad_status s = cuda_check(c, cudaMemcpyAsync(h, c->d_prof_clk, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  if (s == RAD_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream));
+  if (s == RAD_OK)
+    s = cuda_check(c, cudaMemsetAsync(c->d_prof_clk, 0, 2 * sizeof(unsigned long long), c->stream));
+  if (s != RAD_OK) return s;
+  if (h[1] > 0) *sm_mhz = 1e3 * (double)h[0] / (double)h[1];
   return RAD_OK;
 }
 

@@ -45,6 +45,7 @@ struct rad_ctx {
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;  // 3 per timed call
   size_t prof_used = 0;
+  unsigned long long* d_prof_clk = nullptr;  // [2] cycles, ns of the accumulate CTAs
   long long generation = 0;      // bumped whenever d_js changes
   rad_status last_err = RAD_OK;
   bool failed = false;

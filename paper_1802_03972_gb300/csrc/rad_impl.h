@@ -83,26 +83,33 @@ struct LaunchArgs {
   long long n_items;
   unsigned long long* item_counter;
   JobCall inline_call;
+  // Profiling only (else null): [0] SM clock cycles and [1] nanoseconds, each
+  // summed over the accumulate CTAs' lifetimes.
+  unsigned long long* prof_clk;
 };
 
 // Kernel variants of the mixed-precision accumulate kernel.
 struct Variant {
   int threads;
-  int w;  // frequencies per thread
+  int w;       // frequencies per thread and pass
+  int passes;  // frequency passes over each staged particle tile
 };
 // 0-2, 5: FP32-FMA accumulation, w frequencies per thread;
 // 3-4: tensor-core accumulation, a warp covers 32 frequencies (w = 1 in the
-// tiling rules: bins per tile = threads x w, frequency tiles multiples of 32 w);
-// 6: FP32-FMA with the paper's literal sum as well (literal contexts only).
-constexpr int kNumVariants = 7;
+// tiling rules: bins per tile = threads x w x passes, frequency tiles multiples
+// of 32 w passes);
+// 6: FP32-FMA with the paper's literal sum as well (literal contexts only);
+// 7: tensor-core accumulation in two frequency passes per staged particle tile.
+constexpr int kNumVariants = 8;
 constexpr int kLiteralVariant = 6;
 inline Variant variant_info(int v) {
   switch (v) {
-    case 1: return {256, 4};
-    case 2: return {128, 2};
+    case 1: return {256, 4, 1};
+    case 2: return {128, 2, 1};
     case 3:
-    case 4: return {256, 1};
-    default: return {256, 2};
+    case 4: return {256, 1, 1};
+    case 7: return {256, 1, 2};
+    default: return {256, 2, 1};
   }
 }
 cudaError_t launch_readout_literal(const float* state_p, int n_bins, double* out, cudaStream_t s);

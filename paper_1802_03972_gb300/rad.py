@@ -31,7 +31,7 @@ EXPORTS = [
     "rad_batch_sync", "rad_batch_destroy", "rad_server_create", "rad_job_submit", "rad_job_feed",
     "rad_job_finish", "rad_job_poll", "rad_job_result", "rad_server_stats_get",
     "rad_server_destroy", "rad_status_str", "rad_last_error", "rad_kernel_launch_count",
-    "rad_probe_peaks", "rad_profile_enable", "rad_profile_read", "rad_accumulate_static",
+    "rad_probe_peaks", "rad_probe_tensor", "rad_profile_enable", "rad_profile_read", "rad_profile_clock", "rad_accumulate_static",
     "rad_spectrum_literal", "rad_push_step", "rad_push_flush",
 ]
 FF_LITERAL = 2  # rad_ff.flags at creation: also accumulate the paper's literal sum
@@ -119,8 +119,10 @@ def load(path: str = LIB_PATH):
         "rad_last_error": (st, [vp]),
         "rad_kernel_launch_count": (i64, []),
         "rad_probe_peaks": (ctypes.c_int, [vp, ctypes.c_int]),
+        "rad_probe_tensor": (ctypes.c_int, [vp, ctypes.c_int]),
         "rad_profile_enable": (st, [vp, i32]),
         "rad_profile_read": (st, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(i64)]),
+        "rad_profile_clock": (st, [vp, ctypes.POINTER(dbl)]),
         "rad_accumulate_static": (st, [vp, i32, vp, i32, i64, vp, vp, vp, vp, dbl, dbl, vp, vp]),
         "rad_spectrum_literal": (st, [vp, vp]),
         "rad_push_step": (st, [vp, i64, vp, vp, vp, dbl, dbl]),
@@ -181,6 +183,16 @@ def probe_peaks() -> np.ndarray:
     rc = load().rad_probe_peaks(out.ctypes.data, 16)
     if rc != 0:
         raise RuntimeError(f"rad_probe_peaks failed with CUDA error {rc}")
+    return out
+
+
+def probe_tensor() -> np.ndarray:
+    """rad_probe_tensor: [mma.sync TF32 MACs/clk/SM, clocks per tcgen05.mma kind::tf32 at
+    N = 16, 64, 128, 256, kind::f16 at N = 16, 256, probe MHz]."""
+    out = np.zeros(8)
+    rc = load().rad_probe_tensor(out.ctypes.data, 8)
+    if rc != 0:
+        raise RuntimeError(f"rad_probe_tensor failed with CUDA error {rc}")
     return out
 
 
@@ -307,6 +319,12 @@ class Context:
         _check(self._lib.rad_profile_read(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
                "rad_profile_read")
         return a.value, b.value, n.value
+
+    def profile_clock(self) -> float:
+        """Effective SM clock (MHz) of the accumulate kernels since the last call."""
+        m = ctypes.c_double()
+        _check(self._lib.rad_profile_clock(self._h, ctypes.byref(m)), "rad_profile_clock")
+        return m.value
 
 
 def accumulate_static(omega, dirs, r, beta, beta_dot, w, t: float, dt: float, state,

@@ -64,13 +64,24 @@ def small_lwfa(n=2000, n_omega=100, n_side=8, seed=21):
     return wl
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 7])
 def test_lwfa_small_full_grid_all_variants(variant):
     """LWFA-shaped bunch with weights, Gaussian form factor, ragged particle count
     (2000 = 31 x 64 + 16) and ragged frequency tile (100 of 128), 20 steps."""
     wl = small_lwfa()
     ref = spectra_grid(oracle_run(wl, range(20)), wl)
     ctx = gpu_run(wl, range(20), tile=(variant, 0, 0))
+    check(ctx, ref)
+
+
+def test_two_pass_variant_full_width_tile():
+    """Variant 7 sweeps each staged particle tile in two frequency passes: 300
+    frequencies give one 512-wide tile whose second pass is ragged (44 of 256),
+    over 9 directions and a ragged particle count."""
+    wl = small_lwfa(n=1500, n_omega=300, n_side=3, seed=22)
+    ref = spectra_grid(oracle_run(wl, range(6)), wl)
+    ctx = gpu_run(wl, range(6), tile=(7, 512, 0))
+    assert ctx.get_tile()[:2] == (7, 512)
     check(ctx, ref)
 
 
@@ -196,3 +207,17 @@ def test_large_time_offset():
     ref = spectra_grid(oracle_run(shifted, range(4)), shifted)
     ctx = gpu_run(shifted, range(4))
     check(ctx, ref, parts=("tot",))
+
+
+def test_profile_clock_reports_the_kernel_sm_clock():
+    """rad_profile_clock: SM cycles over elapsed time of the profiled accumulate
+    kernels, between 0.3 and 1.1 of the GPU's maximum clock; 0 after a read."""
+    wl = small_lwfa(n=3000, n_omega=128, n_side=8)
+    ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
+    ctx.profile(True)
+    gpu_run(wl, range(4), ctx=ctx)
+    _, acc_ms, calls = ctx.profile_read()
+    mhz = ctx.profile_clock()
+    assert calls == 4 and acc_ms > 0
+    assert 600.0 < mhz < 2300.0, mhz
+    assert ctx.profile_clock() == 0.0
