@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--serve-jobs", type=int, default=24)
     p.add_argument("--serve-load", type=float, default=0.7,
                    help="arrival rate as a fraction of measured capacity")
+    p.add_argument("--serve-policy", default=None,
+                   help="round policy 'P,ROUND_UPDATES' of the serving legs (0 all, 1 oldest, "
+                        "2 least served; default: the library's)")
     p.add_argument("--serve-rate", type=float, default=None,
                    help="fixed arrival rate (jobs/s) instead of --serve-load")
     p.add_argument("--peaks", action="store_true", help="also run the pipe-throughput probe")
@@ -273,7 +276,7 @@ def fifo_latencies(arrivals, work, rate: float):
 
 
 def serve_leg(n_jobs: int, load: float, rate: float | None, steps_range=(5, 20), seed: int = 5,
-              cap: float = 1.6e12, fifo_rates=None):
+              cap: float = 1.6e12, fifo_rates=None, policy=None):
     """Continuous batching: Poisson arrivals of the batched job mix (steps per job
     scaled to steps_range), each job fed step by step from device buffers; p50/p99
     of arrival-to-result latency and the throughput of the window.  `cap` is the
@@ -295,6 +298,8 @@ def serve_leg(n_jobs: int, load: float, rate: float | None, steps_range=(5, 20),
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / lam, n_jobs))
     srv = rad.Server(hbm_budget=150 << 30, max_slots=64)
+    if policy:
+        srv.set_policy(*policy)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ids, fed, done, lat = [None] * n_jobs, [0] * n_jobs, [False] * n_jobs, [None] * n_jobs
@@ -333,7 +338,8 @@ def serve_leg(n_jobs: int, load: float, rate: float | None, steps_range=(5, 20),
            "steps_per_job": list(steps_range), "p50_s": float(np.percentile(lat, 50)),
            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
            "value": float(sum(work)) / makespan, "unit": UNIT, "makespan_s": makespan,
-           "rounds": stats["rounds"], "peak_footprint_bytes": stats["peak_footprint_bytes"]}
+           "rounds": stats["rounds"], "peak_footprint_bytes": stats["peak_footprint_bytes"],
+           "policy": list(policy) if policy else "library default (least served, 2e10 per round)"}
     if fifo_rates:
         out["fifo_one_job_at_a_time"] = {k: fifo_latencies(arrivals, work, r)
                                          for k, r in fifo_rates.items() if r}
@@ -518,12 +524,13 @@ def main():
     if not args.no_serve and rank == 0:
         single = batched["unbatched_value"] if batched else value / world
         fifo = {"mixed_single_job": single, "fp64_plain": fp64["value"] if fp64 else None}
+        pol = tuple(int(float(x)) for x in args.serve_policy.split(",")) if args.serve_policy else None
         served = serve_leg(args.serve_jobs, args.serve_load, args.serve_rate, cap=value / world,
-                           fifo_rates=fifo)
+                           fifo_rates=fifo, policy=pol)
         # the literal arrival rate of the serving workload: 200 jobs/s over a window of
         # 256 arrivals (steps per job scaled further so the backlog drains in seconds)
         served_literal = serve_leg(256, args.serve_load, 200.0, steps_range=(2, 8), seed=6,
-                                   cap=value / world, fifo_rates=fifo)
+                                   cap=value / world, fifo_rates=fifo, policy=pol)
 
     peaks = None
     if args.peaks and rank == 0:

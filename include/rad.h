@@ -269,6 +269,18 @@ typedef struct {
  * jobs admitted at once. */
 rad_status rad_server_create(size_t hbm_budget, int32_t max_slots, void* stream,
                              rad_server** out);
+/* Round policy of the scheduler.  Each round runs one pending step from each
+ * of a set of admitted jobs in one batched launch:
+ *   RAD_SERVE_ALL: every admitted job with a step ready (equal shares);
+ *   RAD_SERVE_OLDEST: jobs in arrival order until the round holds round_updates
+ *     amplitude updates (particles x bins), at least one job;
+ *   RAD_SERVE_LEAST_SERVED (default, round_updates = 2e10): the same in order of
+ *     the updates each job has had so far (new and small jobs first; ties in
+ *     arrival order).
+ * round_updates >= 1 for the last two (ignored for RAD_SERVE_ALL).  Takes effect
+ * from the next round.  RAD_EINVAL for an unknown policy or round_updates < 1. */
+enum { RAD_SERVE_ALL = 0, RAD_SERVE_OLDEST = 1, RAD_SERVE_LEAST_SERVED = 2 };
+rad_status rad_server_set_policy(rad_server* s, int32_t policy, int64_t round_updates);
 /* Copies the grids; the job waits until it can be admitted. RAD_EINVAL if it
  * could never fit the budget. */
 rad_status rad_job_submit(rad_server* s, const rad_job_desc* desc, rad_job_id* id);

@@ -28,13 +28,15 @@ EXPORTS = [
     "rad_create", "rad_accumulate", "rad_spectrum", "rad_spectrum_ff", "rad_sync", "rad_reset",
     "rad_destroy", "rad_state_size", "rad_state_export", "rad_state_import", "rad_state_merge",
     "rad_get_tile", "rad_set_tile", "rad_tune", "rad_batch_create", "rad_batch_accumulate",
-    "rad_batch_sync", "rad_batch_destroy", "rad_server_create", "rad_job_submit", "rad_job_feed",
+    "rad_batch_sync", "rad_batch_destroy", "rad_server_create", "rad_server_set_policy", "rad_job_submit", "rad_job_feed",
     "rad_job_finish", "rad_job_poll", "rad_job_result", "rad_server_stats_get",
     "rad_server_destroy", "rad_status_str", "rad_last_error", "rad_kernel_launch_count",
     "rad_probe_peaks", "rad_probe_tensor", "rad_profile_enable", "rad_profile_read", "rad_profile_clock", "rad_accumulate_static",
     "rad_spectrum_literal", "rad_push_step", "rad_push_flush",
 ]
 FF_LITERAL = 2  # rad_ff.flags at creation: also accumulate the paper's literal sum
+# Round policies of the serving loop (rad_server_set_policy).
+SERVE_ALL, SERVE_OLDEST, SERVE_LEAST_SERVED = 0, 1, 2
 
 # Limits of rad_accumulate_static (include/rad.h).
 STATIC_MAX_OMEGA, STATIC_MAX_DIRS, STATIC_MAX_BINS, STATIC_MAX_PARTICLES = 4096, 4096, 65536, 65536
@@ -108,6 +110,7 @@ def load(path: str = LIB_PATH):
         "rad_batch_sync": (st, [vp]),
         "rad_batch_destroy": (None, [vp]),
         "rad_server_create": (st, [ctypes.c_size_t, i32, vp, ctypes.POINTER(vp)]),
+        "rad_server_set_policy": (st, [vp, i32, i64]),
         "rad_job_submit": (st, [vp, ctypes.POINTER(rad_job_desc), ctypes.POINTER(i64)]),
         "rad_job_feed": (st, [vp, i64, ctypes.POINTER(rad_step)]),
         "rad_job_finish": (st, [vp, i64]),
@@ -387,6 +390,11 @@ class Server:
         _check(lib.rad_server_create(int(hbm_budget), int(max_slots), _stream_handle(stream),
                                      ctypes.byref(h)), "rad_server_create")
         self._h, self._lib = h, lib
+
+    def set_policy(self, policy: int, round_updates: int = 0) -> None:
+        """rad_server_set_policy: SERVE_ALL, SERVE_OLDEST or SERVE_LEAST_SERVED."""
+        _check(self._lib.rad_server_set_policy(self._h, int(policy), int(round_updates)),
+               "rad_server_set_policy")
 
     def submit(self, omega, dirs, ff_kind=FF_POINT, ff_width=0.0, max_particles=1,
                max_queued=2) -> int:

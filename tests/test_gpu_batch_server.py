@@ -120,11 +120,15 @@ def test_tune_keeps_parity():
     assert row_error(ctx.spectrum()[2], ref["tot"]) <= TOL_TOTAL
 
 
-def test_server_results_equal_alone_and_in_the_mix():
+@pytest.mark.parametrize("policy", [(0, 0), (1, 1), (2, 1_000_000)])
+def test_server_results_equal_alone_and_in_the_mix(policy):
     """Jobs submitted at different times, steps fed incrementally, one slot fewer
-    than jobs (admission waits); each result equals the standalone run."""
+    than jobs (admission waits); each result equals the standalone run, under
+    every round policy (all ready jobs; one job per round in arrival order; least
+    served first up to 1e6 updates per round)."""
     wls = small_jobs()
     srv = rad.Server(hbm_budget=8 << 30, max_slots=3)
+    srv.set_policy(*policy)
     ids = []
     fed = [0] * len(wls)
     for j, wl in enumerate(wls):
@@ -152,6 +156,15 @@ def test_server_results_equal_alone_and_in_the_mix():
         assert lat > 0
     st = srv.stats()
     assert st["completed"] == len(wls) and st["submitted"] == len(wls)
+    srv.close()
+
+
+def test_server_policy_arguments():
+    srv = rad.Server(hbm_budget=1 << 30, max_slots=2)
+    for bad in ((3, 10), (-1, 10), (1, 0), (2, -5)):
+        with pytest.raises(rad.RadError):
+            srv.set_policy(*bad)
+    srv.set_policy(rad.SERVE_ALL, 0)
     srv.close()
 
 
