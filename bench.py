@@ -217,6 +217,59 @@ def reference_arm(args, wl):
     print(json.dumps(out), flush=True)
 
 
+def modes_leg(wl, ring_dev, steps_host, upd: int, n_steps: int = 20):
+    """Throughput of the other accumulation modes on the headline workload:
+    the paper's literal sum (FF_LITERAL), in-situ coupling (push_step: beta_dot
+    differenced on the device) and the readout with the direction-dependent 3-D
+    box form factor, each timed with CUDA events on the current stream."""
+    import torch
+
+    from paper_1802_03972_gb300 import rad
+    ring = len(ring_dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {}
+    lit = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width, ff_flags=rad.FF_LITERAL)
+    lit.accumulate(*ring_dev[0], steps_host[0].t, steps_host[0].dt)
+    lit.sync()
+    a, b = ev(), ev()
+    a.record()
+    for k in range(n_steps):
+        st = steps_host[k % ring]
+        lit.accumulate(*ring_dev[k % ring], st.t, st.dt)
+    b.record()
+    torch.cuda.synchronize()
+    out["literal_sum"] = {"value": n_steps * upd / (a.elapsed_time(b) / 1e3), "unit": UNIT,
+                          "steps": n_steps, "tile": list(lit.get_tile())}
+    lit.close()
+    push = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
+    a, b = ev(), ev()
+    a.record()
+    for k in range(n_steps):
+        st = steps_host[k % ring]
+        r, beta, _, w = ring_dev[k % ring]
+        push.push_step(r, beta, w, st.t, st.dt)
+    push.push_flush()
+    b.record()
+    torch.cuda.synchronize()
+    out["push_coupling"] = {"value": n_steps * upd / (a.elapsed_time(b) / 1e3), "unit": UNIT,
+                            "steps": n_steps}
+    bufs = [torch.empty((wl.dirs.shape[0], wl.omega.shape[0]), dtype=torch.float64, device="cuda")
+            for _ in range(3)]
+    times = {}
+    for name, ff in (("readout_1d_ms", (rad.FF_CIC, 0.1e-6)), ("readout_3d_ms", (rad.FF_CIC, 0.1e-6, rad.FF_3D))):
+        push.spectrum(ff=ff, out=bufs)
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(10):
+            push.spectrum(ff=ff, out=bufs)
+        b.record()
+        torch.cuda.synchronize()
+        times[name] = a.elapsed_time(b) / 10
+    out["readout"] = dict(times, bins=int(wl.dirs.shape[0] * wl.omega.shape[0]))
+    push.close()
+    return out
+
+
 def batch_leg(rounds: int, n_jobs: int = 64):
     """64 independent jobs (the batched job mix) advanced one step per round in one
     persistent launch, CUDA-graph replayed; against the same jobs launched one
@@ -473,6 +526,10 @@ def main():
             pinned.append([torch.from_numpy(a).pin_memory() for a in (st.r, st.beta, st.beta_dot, st.w)])
         outs = [np.zeros((wl.dirs.shape[0], wl.omega.shape[0])) for _ in range(3)]
         ectx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
+        if args.tile:
+            ectx.set_tile(*tile)
+        elif not args.no_tune:
+            ectx.tune(wl.n_particles)  # the shape's tuned tile, from the tuner's cache
         ectx.accumulate(*pinned[0], steps_host[0].t, steps_host[0].dt)
         ectx.spectrum(out=outs)
         if dist:
@@ -517,6 +574,10 @@ def main():
         rate, cores, desc, _ = cpu_oracle_rate(wl, 64, 10.0)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
+    modes = None
+    if rank == 0:
+        modes = modes_leg(wl, ring_dev, steps_host, upd)
+
     batched = None
     if not args.no_batch and rank == 0:
         batched = batch_leg(args.batch_rounds)
@@ -549,7 +610,8 @@ def main():
                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(wl),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clocks, "rel_err_sampled": rel_err, "fp64_plain": fp64,
-               "batched": batched, "serving": served, "serving_literal_rate": served_literal,
+               "modes": modes, "batched": batched, "serving": served,
+               "serving_literal_rate": served_literal,
                "p50_s": served["p50_s"] if served else None,
                "p99_s": served["p99_s"] if served else None}
         if peaks:

@@ -42,6 +42,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "rad_device.cuh"
 #include "rad_impl.h"
 
@@ -703,12 +705,14 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
 template <int T, int W, int MINB, bool TC, bool LIT, int P = 1>
 cudaError_t launch_acc(const LaunchArgs& a, int grid, cudaStream_t s) {
   const size_t smem = Smem<T, TC, LIT, P>::bytes;
-  static bool attr_set = false;  // the opt-in is per kernel and idempotent
-  if (!attr_set) {
+  // The shared-memory opt-in is per kernel and device, and idempotent.
+  static std::atomic<bool> attr_set[kMaxDevices];
+  const int dev = current_device();
+  if (dev < 0 || dev >= kMaxDevices || !attr_set[dev].load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    if (dev >= 0 && dev < kMaxDevices) attr_set[dev].store(true, std::memory_order_release);
   }
   accumulate_kernel<T, W, MINB, TC, LIT, P><<<grid, T, smem, s>>>(a);
   count_launches(1);
@@ -746,21 +750,27 @@ size_t accumulate_smem_bytes(int variant) {
 }
 
 int accumulate_blocks_per_sm(int variant) {
-  static int cached[kNumVariants] = {};
+  static std::atomic<int> cached[kMaxDevices][kNumVariants];  // per device; 0 = not yet
   if (variant < 0 || variant >= kNumVariants) variant = 0;
-  if (cached[variant] == 0) {
-    switch (variant) {
-      case 1: cached[1] = blocks_per_sm<256, 4, 2, false, false>(); break;
-      case 2: cached[2] = blocks_per_sm<128, 2, 6, false, false>(); break;
-      case 3: cached[3] = blocks_per_sm<256, 1, 3, true, false>(); break;
-      case 4: cached[4] = blocks_per_sm<256, 1, 4, true, false>(); break;
-      case 5: cached[5] = blocks_per_sm<256, 2, 4, false, false>(); break;
-      case 6: cached[6] = blocks_per_sm<256, 2, 2, false, true>(); break;
-      case 7: cached[7] = blocks_per_sm<256, 1, 3, true, false, 2>(); break;
-      default: cached[0] = blocks_per_sm<256, 2, 3, false, false>(); break;
-    }
+  const int dev = current_device();
+  const bool cache = dev >= 0 && dev < kMaxDevices;
+  if (cache) {
+    const int c = cached[dev][variant].load(std::memory_order_relaxed);
+    if (c > 0) return c;
   }
-  return cached[variant];
+  int nb;
+  switch (variant) {
+    case 1: nb = blocks_per_sm<256, 4, 2, false, false>(); break;
+    case 2: nb = blocks_per_sm<128, 2, 6, false, false>(); break;
+    case 3: nb = blocks_per_sm<256, 1, 3, true, false>(); break;
+    case 4: nb = blocks_per_sm<256, 1, 4, true, false>(); break;
+    case 5: nb = blocks_per_sm<256, 2, 4, false, false>(); break;
+    case 6: nb = blocks_per_sm<256, 2, 2, false, true>(); break;
+    case 7: nb = blocks_per_sm<256, 1, 3, true, false, 2>(); break;
+    default: nb = blocks_per_sm<256, 2, 3, false, false>(); break;
+  }
+  if (cache) cached[dev][variant].store(nb, std::memory_order_relaxed);
+  return nb;
 }
 
 cudaError_t launch_accumulate(int variant, const LaunchArgs& a, int grid, cudaStream_t s) {

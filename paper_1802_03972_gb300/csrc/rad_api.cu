@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <new>
 #include <vector>
@@ -38,13 +39,19 @@ bool is_device_ptr(const void* p) {
 }
 
 int device_sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
+  static std::atomic<int> cached[kMaxDevices];  // per device; 0 = not yet
+  const int dev = current_device();
+  const bool cache = dev >= 0 && dev < kMaxDevices;
+  if (cache) {
+    const int c = cached[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
   }
+  int n = 0;
+  if (dev < 0 || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (cache) cached[dev].store(n, std::memory_order_relaxed);
   return n;
 }
 
@@ -58,6 +65,15 @@ cudaError_t dmalloc(T** p, size_t count) {
 }  // namespace
 
 namespace radimpl {
+
+int current_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return dev;
+}
 
 rad_status fail(rad_ctx* c, rad_status s) {
   if (c) {
@@ -334,8 +350,8 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
   c->ff = ff;
   c->prec = prec;
   c->stream = (cudaStream_t)stream;
-  c->tile.variant = 0;
-  c->tile.omega_tile = default_omega_tile(0, n_omega);
+  c->tile.variant = kDefaultVariant;
+  c->tile.omega_tile = default_omega_tile(kDefaultVariant, n_omega);
   c->tile.chunk = 0;
 
   // Frequency table: omega/2pi split hi/lo; (hi, -hi, 2pi hi, 2pi lo) floats.

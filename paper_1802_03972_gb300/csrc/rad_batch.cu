@@ -97,10 +97,10 @@ void BatchCore::invalidate_graphs() {
 // Enqueue one round.  jobs[i] receives steps[i]; n = 0 skips a job.
 rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_jobs, bool use_graphs) {
   if (n_jobs > cap) return RAD_EINVAL;
-  // Variant: the jobs' common variant, else 0.
+  // Variant: the jobs' common variant, else the default one.
   int variant = jobs[0]->tile.variant;
   for (int i = 1; i < n_jobs; ++i)
-    if (jobs[i]->tile.variant != variant) variant = 0;
+    if (jobs[i]->tile.variant != variant) variant = kDefaultVariant;
 
   // Per-job chunking, capacities (may reallocate: drain this stream first).
   struct Plan { int job; long long n; int ck, n_chunks; long long cost; JobStatic js; };

@@ -102,6 +102,7 @@ struct Variant {
 // 7: tensor-core accumulation in two frequency passes per staged particle tile.
 constexpr int kNumVariants = 8;
 constexpr int kLiteralVariant = 6;
+constexpr int kDefaultVariant = 7;  // a new context's tile, and a mixed batch's
 inline Variant variant_info(int v) {
   switch (v) {
     case 1: return {256, 4, 1};
@@ -118,6 +119,10 @@ cudaError_t launch_readout_literal(const float* state_p, int n_bins, double* out
 cudaError_t launch_prepass(const LaunchArgs& a, int total_blocks, cudaStream_t s);
 cudaError_t launch_accumulate(int variant, const LaunchArgs& a, int grid, cudaStream_t s);
 int accumulate_blocks_per_sm(int variant);
+// Per-device caches of launch properties cover device ordinals below this.
+constexpr int kMaxDevices = 64;
+// The calling thread's current device, or -1 (rad_api.cu).
+int current_device();
 size_t accumulate_smem_bytes(int variant);
 cudaError_t launch_readout(const float* state, int mixed, const double* state64, int n_omega,
                            int n_bins, const double* omega, const double* dirs, rad_ff ff,

@@ -77,3 +77,22 @@ def test_literal_checkpoint_and_restrictions():
         rad.Batch([a])                    # literal contexts run on their own
     with pytest.raises(rad.RadError):
         rad.Context(wl.omega, wl.dirs, rad.FF_CIC, 0.1e-6, prec=rad.PREC_FP64, ff_flags=rad.FF_LITERAL)
+
+
+def test_literal_merge_of_particle_shards():
+    """Two contexts fed disjoint halves of the particles, merged (rad_state_merge),
+    give the literal sum of one context fed all of them (amplitudes add before
+    |.|^2; up to the order of floating-point sums)."""
+    wl = inputs.lwfa_bunch(n_particles=1200, n_omega=64, n_side=4, seed=64)
+    full = run_literal(wl, range(4))
+    halves = []
+    for lo, hi in ((0, 600), (600, 1200)):
+        ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width, ff_flags=rad.FF_LITERAL)
+        for s in range(4):
+            st = wl.step(s)
+            cut = [to_dev(a.reshape(3, -1)[:, lo:hi].ravel()) for a in (st.r, st.beta, st.beta_dot)]
+            ctx.accumulate(*cut, to_dev(st.w[lo:hi]), st.t, st.dt)
+        halves.append(ctx)
+    halves[0].state_merge(halves[1].state_export())
+    assert row_error(halves[0].spectrum_literal(), full.spectrum_literal()) <= 1e-6
+    assert row_error(halves[0].spectrum()[2], full.spectrum()[2]) <= 1e-6
