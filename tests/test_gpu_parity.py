@@ -111,11 +111,14 @@ def test_readout_3d_box_form_factor():
 
 def test_lwfa_full_size_sampled_rows():
     """Full LWFA size (1e5 macro-particles, 512 log omega, 16 x 16 directions) in the
-    benchmark's launch configuration, 4 steps; the oracle computes 3 sampled
-    directions over all 512 frequencies (the gated per-direction error)."""
+    benchmark's launch configuration (the tile rad_tune picks for this shape, as the
+    benchmark uses it), 4 steps; the oracle computes 3 sampled directions over all
+    512 frequencies (the gated per-direction error)."""
     wl = inputs.lwfa_bunch()
     steps = range(0, 4)
-    ctx = gpu_run(wl, steps)
+    ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
+    ctx.tune(wl.n_particles)
+    gpu_run(wl, steps, ctx=ctx)
     coh, inc, tot = ctx.spectrum()
     rows = [0, 137, 255]
     bins = [(d, o) for d in rows for o in range(512)]
