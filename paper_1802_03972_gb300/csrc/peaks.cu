@@ -14,11 +14,16 @@ namespace {
 
 constexpr int kThreads = 512;
 
+// Block b records its start and end SM cycle counts and the SM it ran on in
+// cyc[3b .. 3b + 2]; the host rates each SM over the span of all its blocks.
 __device__ __forceinline__ void stamp(long long* cyc, long long t0) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    cyc[2 * blockIdx.x] = t0;
-    cyc[2 * blockIdx.x + 1] = clock64();
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    cyc[3 * blockIdx.x] = t0;
+    cyc[3 * blockIdx.x + 1] = clock64();
+    cyc[3 * blockIdx.x + 2] = (long long)sm;
   }
 }
 
@@ -203,11 +208,7 @@ __global__ void __launch_bounds__(256) k_mma_sync(float* out, long long* cyc, in
 #pragma unroll
   for (int j = 0; j < 4; ++j) s += d[j][0] + d[j][1] + d[j][2] + d[j][3];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    cyc[2 * blockIdx.x] = t0;
-    cyc[2 * blockIdx.x + 1] = clock64();
-  }
+  stamp(cyc, t0);
 }
 
 // Instruction descriptor of tcgen05.mma, dense, FP32 accumulator, K-major A and
@@ -281,6 +282,41 @@ __global__ void __launch_bounds__(32, 1) k_umma(int n_mma, long long* cyc, int* 
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tb) : "memory");
 }
 
+// Operations per SM clock and the effective clock (MHz) of a probe launch of
+// nb blocks, each doing ops_per_block operations: every SM is timed from its
+// first block's start to its last block's end, so blocks that an SM ran one
+// after another are not counted as concurrent.
+void rate_per_sm(const long long* h, int nb, double ops_per_block, float ms, int n_sm_max,
+                 double* rate, double* mhz) {
+  long long* first = new long long[n_sm_max];
+  long long* last = new long long[n_sm_max];
+  int* cnt = new int[n_sm_max];
+  for (int i = 0; i < n_sm_max; ++i) {
+    cnt[i] = 0;
+    first[i] = last[i] = 0;
+  }
+  for (int b = 0; b < nb; ++b) {
+    const long long sm = h[3 * b + 2];
+    if (sm < 0 || sm >= n_sm_max) continue;
+    if (cnt[sm] == 0 || h[3 * b] < first[sm]) first[sm] = h[3 * b];
+    if (cnt[sm] == 0 || h[3 * b + 1] > last[sm]) last[sm] = h[3 * b + 1];
+    cnt[sm]++;
+  }
+  double ops = 0.0, span = 0.0;
+  int sms = 0;
+  for (int i = 0; i < n_sm_max; ++i) {
+    if (cnt[i] == 0) continue;
+    ops += ops_per_block * cnt[i];
+    span += (double)(last[i] - first[i]);
+    sms++;
+  }
+  *rate = span > 0 ? ops / span : 0.0;
+  *mhz = sms > 0 && ms > 0 ? span / sms / (ms * 1e-3) / 1e6 : 0.0;
+  delete[] first;
+  delete[] last;
+  delete[] cnt;
+}
+
 }  // namespace
 
 extern "C" {
@@ -306,9 +342,12 @@ int rad_probe_peaks(double* out, int n_out) {
   long long* d_cyc = nullptr;
   cudaError_t e = cudaMalloc(&d_out, sizeof(float) * blocks * kThreads);
   if (e != cudaSuccess) return (int)e;
-  e = cudaMalloc(&d_cyc, sizeof(long long) * 2 * blocks);
+  e = cudaMalloc(&d_cyc, sizeof(long long) * 3 * blocks);
   if (e != cudaSuccess) { cudaFree(d_out); return (int)e; }
-  long long* h_cyc = new long long[2 * blocks];
+  long long* h_cyc = new long long[3 * blocks];
+  int sm_ids = 0;  // %smid may exceed the SM count; bound it by the attribute
+  cudaDeviceGetAttribute(&sm_ids, cudaDevAttrMultiProcessorCount, dev);
+  sm_ids = 2 * sm_ids + 64;
   cudaEvent_t ev0, ev1;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
@@ -326,13 +365,8 @@ int rad_probe_peaks(double* out, int n_out) {
     cudaEventSynchronize(ev1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
-    cudaMemcpy(h_cyc, d_cyc, sizeof(long long) * 2 * nb, cudaMemcpyDeviceToHost);
-    double cyc_sum = 0.0;
-    for (int b = 0; b < nb; ++b) cyc_sum += (double)(h_cyc[2 * b + 1] - h_cyc[2 * b]);
-    const double cyc_mean = cyc_sum / nb;
-    const double ops_per_sm = ops_per_thread * kThreads * per_sm;
-    res[0] = ops_per_sm / cyc_mean;
-    res[1] = cyc_mean / (ms * 1e-3) / 1e6;
+    cudaMemcpy(h_cyc, d_cyc, sizeof(long long) * 3 * nb, cudaMemcpyDeviceToHost);
+    rate_per_sm(h_cyc, nb, ops_per_thread * kThreads, ms, sm_ids, &res[0], &res[1]);
   };
 
   const int it = 1 << 14;
@@ -369,10 +403,11 @@ int rad_probe_tensor(double* out, int n_out) {
   long long* d_cyc = nullptr;
   int* d_err = nullptr;
   cudaError_t e = cudaMalloc(&d_out, sizeof(float) * blocks * 256);
-  if (e == cudaSuccess) e = cudaMalloc(&d_cyc, sizeof(long long) * 2 * blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&d_cyc, sizeof(long long) * 3 * blocks);
   if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(int));
-  long long* h_cyc = new long long[2 * blocks];
+  long long* h_cyc = new long long[3 * blocks];
+  const int sm_ids = 2 * n_sm + 64;
   cudaEvent_t ev0, ev1;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
@@ -385,13 +420,9 @@ int rad_probe_tensor(double* out, int n_out) {
     cudaEventSynchronize(ev1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
-    cudaMemcpy(h_cyc, d_cyc, sizeof(long long) * 2 * blocks, cudaMemcpyDeviceToHost);
-    double cyc_sum = 0.0;
-    for (int b = 0; b < blocks; ++b) cyc_sum += (double)(h_cyc[2 * b + 1] - h_cyc[2 * b]);
-    const double cyc_mean = cyc_sum / blocks;
-    const double macs_per_sm = (double)per_sm * 8 * iters * 4 * 16 * 8 * 8;
-    out[0] = macs_per_sm / cyc_mean;
-    out[7] = cyc_mean / (ms * 1e-3) / 1e6;
+    cudaMemcpy(h_cyc, d_cyc, sizeof(long long) * 3 * blocks, cudaMemcpyDeviceToHost);
+    // multiply-adds per block: 8 warps x iters x 4 MMAs x (16 x 8 x 8)
+    rate_per_sm(h_cyc, blocks, 8.0 * iters * 4 * 16 * 8 * 8, ms, sm_ids, &out[0], &out[7]);
   }
   auto umma = [&](auto kern, double* res) {
     if (e != cudaSuccess) return;
