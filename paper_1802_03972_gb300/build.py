@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librad.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["rad_kernels.cu", "rad_accumulate.cu", "rad_api.cu", "rad_batch.cu", "rad_tune.cu",
-           "rad_server.cu", "rad_static.cu", "rad_push.cu", "peaks.cu"]
+           "rad_server.cu", "rad_static.cu", "rad_push.cu", "rad_selftest.cu", "peaks.cu"]
 
 
 def nvcc() -> str:

@@ -494,6 +494,7 @@ void rad_destroy(rad_ctx* c) {
 
 rad_status rad_accumulate(rad_ctx* c, int64_t n, const double* r, const double* beta,
                           const double* beta_dot, const double* w, double t, double dt) {
+  radimpl::TraceRange trace("rad_accumulate");
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
   if (n < 0 || !isfinite(t) || !isfinite(dt) || !(dt > 0.0)) return fail(c, RAD_EINVAL);
@@ -535,6 +536,7 @@ rad_status rad_sync(rad_ctx* c) {
 }
 
 rad_status rad_spectrum_ff(rad_ctx* c, rad_ff ff, double* coh, double* inc, double* tot) {
+  radimpl::TraceRange trace("rad_spectrum");
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
   // RAD_FF_LITERAL only matters at creation; the readout ignores it.
@@ -584,6 +586,7 @@ rad_status rad_reset(rad_ctx* c) {
 }
 
 rad_status rad_spectrum_literal(rad_ctx* c, double* out) {
+  radimpl::TraceRange trace("rad_spectrum_literal");
   if (!c || !out) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
   if (!c->d_state_p) return fail(c, RAD_ESTATE);

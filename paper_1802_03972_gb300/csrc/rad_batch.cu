@@ -279,6 +279,7 @@ rad_status rad_batch_accumulate(rad_batch* b, const rad_step* steps) {
     if (st.n > 0 && (!st.r || !st.beta || !st.beta_dot || !st.w)) return RAD_EINVAL;
     if (b->jobs[i]->failed) return RAD_ESTATE;
   }
+  TraceRange trace("rad_batch_accumulate");
   rad_status s = b->core.run(b->jobs.data(), steps, (int)b->jobs.size(), true);
   if (s == RAD_ECUDA) b->failed = true;
   return s;

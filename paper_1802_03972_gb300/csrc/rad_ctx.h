@@ -5,6 +5,8 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rad.h"
 #include "rad_impl.h"
 
@@ -52,6 +54,15 @@ struct rad_ctx {
 };
 
 namespace radimpl {
+
+// A named NVTX range for the enclosing scope (host side; shows the library's
+// calls on a profiler timeline, a no-op when no tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 rad_status fail(rad_ctx* c, rad_status s);
 rad_status cuda_check(rad_ctx* c, cudaError_t e);

@@ -40,8 +40,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Waits for the given phase parity of the barrier; gives up after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+// Waits for the given phase parity of the barrier; gives up after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
   const uint32_t a = smem_addr(bar);
   const unsigned long long t0 = global_ns();
   for (;;) {
@@ -51,7 +52,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done) : "r"(a), "r"(phase) : "memory");
     if (done) return true;
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 // One elected thread: bulk copy of `bytes` (multiple of 16, both addresses

@@ -37,15 +37,6 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-bool device_ptr(const void* p) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
 struct Slot {
   double* d = nullptr;       // [10 * max_particles]: r, beta, beta_dot, w
   cudaEvent_t ready = nullptr;
@@ -243,6 +234,7 @@ void rad_server::loop() {
     lk.unlock();
     rad_status rs = RAD_OK;
     if (!ctxs.empty()) {
+      TraceRange trace("rad_server round");
       rs = core.run(ctxs.data(), steps.data(), (int)ctxs.size(), false);
       if (rs == RAD_OK && cudaStreamSynchronize(compute) != cudaSuccess) rs = RAD_ECUDA;
     }
@@ -390,21 +382,30 @@ rad_status rad_job_feed(rad_server* s, rad_job_id id, const rad_step* step) {
     int k = 0;
     while (k < (int)j.slots.size() && j.slots[k].busy) ++k;
     if (k == (int)j.slots.size()) return RAD_EBUSY;
+    // Reserve the slot, then copy without holding the lock, so the scheduler
+    // keeps forming rounds meanwhile.  The job cannot be released while this
+    // step is outstanding: it is not finished (checked above), and callers use
+    // a server from one thread at a time.
     Slot& sl = j.slots[k];
+    sl.busy = true;
+    double* dst = sl.d;
+    cudaEvent_t ready = sl.ready;
+    lk.unlock();
+    cudaError_t e = cudaSuccess;
     size_t off = 0;
-    for (int i = 0; i < 4; ++i) {
-      if (cudaMemcpyAsync(sl.d + off, src[i], cnt[i] * sizeof(double), cudaMemcpyDefault,
-                          s->copy) != cudaSuccess)
-        return RAD_ECUDA;
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+      e = cudaMemcpyAsync(dst + off, src[i], cnt[i] * sizeof(double), cudaMemcpyDefault, s->copy);
       off += cnt[i];
     }
-    if (cudaEventRecord(sl.ready, s->copy) != cudaSuccess) return RAD_ECUDA;
-    // The caller may reuse its buffers on return.
-    const bool host_src = !(device_ptr(step->r) && device_ptr(step->beta) &&
-                            device_ptr(step->beta_dot) && device_ptr(step->w));
-    if (host_src && cudaEventSynchronize(sl.ready) != cudaSuccess) return RAD_ECUDA;
-    if (!host_src && cudaEventSynchronize(sl.ready) != cudaSuccess) return RAD_ECUDA;
-    sl.busy = true;
+    if (e == cudaSuccess) e = cudaEventRecord(ready, s->copy);
+    // The caller may reuse its buffers on return, host or device.
+    if (e == cudaSuccess) e = cudaEventSynchronize(ready);
+    lk.lock();
+    if (e != cudaSuccess || j.state != JobState::Active) {
+      sl.busy = false;
+      if (e != cudaSuccess) return RAD_ECUDA;
+      return j.err == RAD_OK ? RAD_ESTATE : j.err;
+    }
     q.slot = k;
   }
   j.queue.push_back(std::move(q));

@@ -1,0 +1,105 @@
+// Per-(particle, direction) and per-update arithmetic of the accumulate
+// kernel, shared with the self-test kernels that check it against FP64 host
+// values: stage 1 (retarded-time offset and transverse amplitude of one
+// particle record for one direction) and the exact phase reduction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rad_device.cuh"
+
+namespace radimpl {
+namespace dev {
+
+// Stage 1: record of (particle, direction).  raw: the particle's 80-byte record.
+// Returns false when |dtau| is beyond the fast phase path's range.
+__device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
+                                               const float* __restrict__ dt_, int n_dir, int d,
+                                               float tau_fast, float& th, float& tl, float amp[4]) {
+  const float4 q0 = *reinterpret_cast<const float4*>(raw);
+  const float4 q1 = *reinterpret_cast<const float4*>(raw + 4);
+  const float4 q2 = *reinterpret_cast<const float4*>(raw + 8);
+  const float4 q3 = *reinterpret_cast<const float4*>(raw + 12);
+  const float2 q4 = *reinterpret_cast<const float2*>(raw + 16);
+  const float sh0 = q0.x, sh1 = q0.y, sh2 = q0.z, sl0 = q0.w, sl1 = q1.x, sl2 = q1.y;
+  const float bh0 = q1.z, bh1 = q1.w, bh2 = q2.x, bl0 = q2.y, bl1 = q2.z, bl2 = q2.w;
+  const float ad0 = q3.x, ad1 = q3.y, ad2 = q3.z, g2 = q3.w, ww = q4.x, sw = q4.y;
+  const float nh0 = __ldg(dt_ + 0 * n_dir + d), nh1 = __ldg(dt_ + 1 * n_dir + d), nh2 = __ldg(dt_ + 2 * n_dir + d);
+  const float nl0 = __ldg(dt_ + 3 * n_dir + d), nl1 = __ldg(dt_ + 4 * n_dir + d), nl2 = __ldg(dt_ + 5 * n_dir + d);
+  const float e10 = __ldg(dt_ + 6 * n_dir + d), e11 = __ldg(dt_ + 7 * n_dir + d), e12 = __ldg(dt_ + 8 * n_dir + d);
+  const float e20 = __ldg(dt_ + 9 * n_dir + d), e21 = __ldg(dt_ + 10 * n_dir + d), e22 = __ldg(dt_ + 11 * n_dir + d);
+
+  // n . s in float-float: exact products (TwoProduct via fma) and exact sums
+  // (Knuth TwoSum) of the hi parts, all first-order lo terms added in FP32.
+  const float p0 = __fmul_rn(nh0, sh0), p1 = __fmul_rn(nh1, sh1), p2 = __fmul_rn(nh2, sh2);
+  float lo = __fadd_rn(__fadd_rn(fmaf(nh0, sh0, -p0), fmaf(nh1, sh1, -p1)), fmaf(nh2, sh2, -p2));
+  lo = fmaf(nh0, sl0, lo);
+  lo = fmaf(nh1, sl1, lo);
+  lo = fmaf(nh2, sl2, lo);
+  lo = fmaf(nl0, sh0, lo);
+  lo = fmaf(nl1, sh1, lo);
+  lo = fmaf(nl2, sh2, lo);
+  const float s1 = __fadd_rn(p0, p1);
+  float bb = __fsub_rn(s1, p0);
+  const float er1 = __fadd_rn(__fsub_rn(p0, __fsub_rn(s1, bb)), __fsub_rn(p1, bb));
+  const float s2 = __fadd_rn(s1, p2);
+  bb = __fsub_rn(s2, s1);
+  const float er2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, bb)), __fsub_rn(p2, bb));
+  lo = __fadd_rn(lo, __fadd_rn(er1, er2));
+  const float hi = __fadd_rn(s2, lo);
+  const float lo2 = __fsub_rn(lo, __fsub_rn(hi, s2));
+  th = -hi;
+  tl = -lo2;
+
+  // Transverse amplitude (see the file comment).
+  const float b1 = fmaf(e10, bh0, fmaf(e11, bh1, e12 * bh2)) + fmaf(e10, bl0, fmaf(e11, bl1, e12 * bl2));
+  const float b2 = fmaf(e20, bh0, fmaf(e21, bh1, e22 * bh2)) + fmaf(e20, bl0, fmaf(e21, bl1, e22 * bl2));
+  const float bn = fmaf(nh0, bh0, fmaf(nh1, bh1, nh2 * bh2));
+  const float d1 = fmaf(e10, ad0, fmaf(e11, ad1, e12 * ad2));
+  const float d2 = fmaf(e20, ad0, fmaf(e21, ad1, e22 * ad2));
+  const float dn = fmaf(nh0, ad0, fmaf(nh1, ad1, nh2 * ad2));
+  const float D = (g2 + fmaf(b1, b1, b2 * b2)) / (1.0f + bn);
+  const float iD = 1.0f / D;
+  const float iD2 = iD * iD;
+  const float a1 = -fmaf(b1, dn, d1 * D) * iD2;
+  const float a2 = -fmaf(b2, dn, d2 * D) * iD2;
+  amp[0] = ww * a1;  // U . e1
+  amp[1] = ww * a2;  // U . e2
+  amp[2] = sw * a1;  // V . e1
+  amp[3] = sw * a2;  // V . e2
+  return fabsf(th) <= tau_fast;  // false for NaN as well
+}
+
+// Shared memory: one raw particle tile (THREADS x 80 B, TMA destination) and
+// two record buffers.  FP32 variants: per record 3 float4 (values duplicated
+// for packed arithmetic); tensor-core variants: float2 dtau + 8 floats of
+// amplitude hi/lo parts.
+// Tensor-core variants also keep their per-chunk (second-level) sums in
+// shared memory: 16 floats per thread, one slot per thread and value.
+// The literal variant adds a fourth float4 per record: (w - 1) duplicated.
+
+// Phase of a frequency pair (packed) for one particle: returns radians in
+// (-pi, pi] + a tiny cross-term excess.
+__device__ __forceinline__ float2 phase2(float2 omh, float2 nomh, float2 wh, float2 wl, float2 th,
+                                         float2 tl) {
+  const float2 kMag = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23
+  const float2 kNegMag = make_float2(-12582912.0f, -12582912.0f);
+  const float2 k2Pi = make_float2(6.28318530717958647692f, 6.28318530717958647692f);
+  const float2 t0 = __ffma2_rn(nomh, th, kMag);  // 1.5*2^23 - rint(x)
+  const float2 q = __fadd2_rn(t0, kNegMag);       // -rint(x), exact
+  const float2 f0 = __ffma2_rn(omh, th, q);       // x - rint(x), one rounding
+  const float2 c1 = __fmul2_rn(wl, th);           // cross terms, radians
+  const float2 c2 = __ffma2_rn(wh, tl, c1);
+  return __ffma2_rn(f0, k2Pi, c2);
+}
+
+// Phase in FP64 (wide path): omega/2pi times the float-float dtau, reduced.
+__device__ __forceinline__ float phase_wide(double om_turns, float th, float tl) {
+  double x = om_turns * ((double)th + (double)tl);
+  x -= rint(x);
+  return (float)(x * 6.283185307179586);
+}
+
+}  // namespace dev
+}  // namespace radimpl

@@ -33,6 +33,7 @@ EXPORTS = [
     "rad_server_destroy", "rad_status_str", "rad_last_error", "rad_kernel_launch_count",
     "rad_probe_peaks", "rad_probe_tensor", "rad_profile_enable", "rad_profile_read", "rad_profile_clock", "rad_accumulate_static",
     "rad_spectrum_literal", "rad_push_step", "rad_push_flush",
+    "rad_selftest_wait", "rad_selftest_stage1", "rad_selftest_phase",
 ]
 FF_LITERAL = 2  # rad_ff.flags at creation: also accumulate the paper's literal sum
 # Round policies of the serving loop (rad_server_set_policy).
@@ -126,6 +127,9 @@ def load(path: str = LIB_PATH):
         "rad_profile_enable": (st, [vp, i32]),
         "rad_profile_read": (st, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(i64)]),
         "rad_profile_clock": (st, [vp, ctypes.POINTER(dbl)]),
+        "rad_selftest_wait": (st, [i64, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
+        "rad_selftest_stage1": (st, [vp, i64, vp, vp, vp, vp, dbl, dbl, i32, vp, vp]),
+        "rad_selftest_phase": (st, [vp, i32, vp, vp, vp, vp]),
         "rad_accumulate_static": (st, [vp, i32, vp, i32, i64, vp, vp, vp, vp, dbl, dbl, vp, vp]),
         "rad_spectrum_literal": (st, [vp, vp]),
         "rad_push_step": (st, [vp, i64, vp, vp, vp, dbl, dbl]),
@@ -187,6 +191,14 @@ def probe_peaks() -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"rad_probe_peaks failed with CUDA error {rc}")
     return out
+
+
+def selftest_wait(limit_ns: int) -> tuple:
+    """rad_selftest_wait: (timed_out, waited_s) of a bounded wait nothing completes."""
+    flag, waited = ctypes.c_int32(), ctypes.c_double()
+    _check(load().rad_selftest_wait(int(limit_ns), ctypes.byref(flag), ctypes.byref(waited)),
+           "rad_selftest_wait")
+    return bool(flag.value), waited.value
 
 
 def probe_tensor() -> np.ndarray:
@@ -323,6 +335,27 @@ class Context:
                "rad_profile_read")
         return a.value, b.value, n.value
 
+    def selftest_stage1(self, r, beta, beta_dot, w, t: float, dt: float, direction: int):
+        """rad_selftest_stage1: per particle (th, tl, a0..a3, fast, 0) for one direction
+        (device arrays) and the direction's transverse basis (e1, e2)."""
+        n = int(w.shape[0])
+        out = np.zeros((n, 8), dtype=np.float32)
+        basis = np.zeros(6, dtype=np.float32)
+        _check(self._lib.rad_selftest_stage1(self._h, n, _ptr(r), _ptr(beta), _ptr(beta_dot), _ptr(w),
+                                             float(t), float(dt), int(direction), out.ctypes.data,
+                                             basis.ctypes.data), "rad_selftest_stage1")
+        return out, basis.reshape(2, 3)
+
+    def selftest_phase(self, th, tl):
+        """rad_selftest_phase: (fast, wide) phases in radians, [n_omega][len(th)]."""
+        th = np.ascontiguousarray(th, dtype=np.float32)
+        tl = np.ascontiguousarray(tl, dtype=np.float32)
+        fast = np.zeros((self.n_omega, th.shape[0]), dtype=np.float32)
+        wide = np.zeros_like(fast)
+        _check(self._lib.rad_selftest_phase(self._h, th.shape[0], th.ctypes.data, tl.ctypes.data,
+                                            fast.ctypes.data, wide.ctypes.data), "rad_selftest_phase")
+        return fast, wide
+
     def profile_clock(self) -> float:
         """Effective SM clock (MHz) of the accumulate kernels since the last call."""
         m = ctypes.c_double()
@@ -347,7 +380,12 @@ def accumulate_static(omega, dirs, r, beta, beta_dot, w, t: float, dt: float, st
 
 
 def make_step(n, r, beta, beta_dot, w, t, dt) -> rad_step:
-    return rad_step(int(n), _ptr(r), _ptr(beta), _ptr(beta_dot), _ptr(w), float(t), float(dt))
+    """A rad_step pointing at the four arrays (float64, contiguous; host or device).  The
+    step keeps references to them, so they stay alive as long as the step does."""
+    _check_particles(int(n), r, beta, beta_dot, w)
+    st = rad_step(int(n), _ptr(r), _ptr(beta), _ptr(beta_dot), _ptr(w), float(t), float(dt))
+    st._keep = (r, beta, beta_dot, w)
+    return st
 
 
 class Batch:
@@ -421,11 +459,16 @@ class Server:
         _check(self._lib.rad_job_poll(self._h, int(job), ctypes.byref(d)), "rad_job_poll")
         return bool(d.value)
 
-    def result(self, job: int, n_dir: int, n_omega: int, timeout: float = -1.0):
+    def result(self, job: int, n_dir: int, n_omega: int, timeout: float = -1.0,
+               accept_edata: bool = False):
+        """(coherent, incoherent, total, latency_s).  A job that saw invalid particles
+        (RAD_EDATA) raises unless accept_edata; its spectrum then covers the valid ones."""
         outs = [np.zeros((n_dir, n_omega)) for _ in range(3)]
         lat = ctypes.c_double()
-        _check(self._lib.rad_job_result(self._h, int(job), float(timeout), *[o.ctypes.data for o in outs],
-                                        ctypes.byref(lat)), "rad_job_result")
+        st = self._lib.rad_job_result(self._h, int(job), float(timeout), *[o.ctypes.data for o in outs],
+                                      ctypes.byref(lat))
+        if not (accept_edata and st == RAD_EDATA):
+            _check(st, "rad_job_result")
         return outs[0], outs[1], outs[2], lat.value
 
     def stats(self) -> dict:
