@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--serve-jobs", type=int, default=24)
     p.add_argument("--serve-load", type=float, default=0.7,
                    help="arrival rate as a fraction of measured capacity")
+    p.add_argument("--no-modes", action="store_true",
+                   help="skip the literal-sum, in-situ coupling and 3-D readout timings")
     p.add_argument("--serve-policy", default=None,
                    help="round policy 'P,ROUND_UPDATES' of the serving legs (0 all, 1 oldest, "
                         "2 least served; default: the library's)")
@@ -575,7 +577,7 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
     modes = None
-    if rank == 0:
+    if rank == 0 and not args.no_modes:
         modes = modes_leg(wl, ring_dev, steps_host, upd)
 
     batched = None

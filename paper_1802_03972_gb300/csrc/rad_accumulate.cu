@@ -495,20 +495,27 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
       const int o_warp = o_warp0 + ps * PW;
       if (PASSES > 1) load_omega(o_warp);
       if (!(flags & 1)) {
+        auto fast_loop = [&](const int kend) {
 #pragma unroll 2
-        for (int kk = 0; kk < kn8; kk += 8) {
-          const float2 tA = tw[kk + c], tB = tw[kk + c + 4];
-          const uint32_t b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
-          const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
-          const float2 thA = make_float2(tA.x, tA.x), tlA = make_float2(tA.y, tA.y);
-          const float2 thB = make_float2(tB.x, tB.x), tlB = make_float2(tB.y, tB.y);
+          for (int kk = 0; kk < kend; kk += 8) {
+            const float2 tA = tw[kk + c], tB = tw[kk + c + 4];
+            const uint32_t b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
+            const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
+            const float2 thA = make_float2(tA.x, tA.x), tlA = make_float2(tA.y, tA.y);
+            const float2 thB = make_float2(tB.x, tB.x), tlB = make_float2(tB.y, tB.y);
 #pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            const float2 pA = phase2(omh[b], nomh[b], wh[b], wl[b], thA, tlA);
-            const float2 pB = phase2(omh[b], nomh[b], wh[b], wl[b], thB, tlB);
-            tc_block(pA, pB, b0, b1, dre[b], dim[b]);
+            for (int b = 0; b < NB; ++b) {
+              const float2 pA = phase2(omh[b], nomh[b], wh[b], wl[b], thA, tlA);
+              const float2 pB = phase2(omh[b], nomh[b], wh[b], wl[b], thB, tlB);
+              tc_block(pA, pB, b0, b1, dre[b], dim[b]);
+            }
           }
-        }
+        };
+        // A full tile of one direction takes the loop with its trip count known at
+        // compile time (measured ~1 % faster); ragged and multi-direction tiles
+        // the runtime bound.
+        if (kn8 == THREADS) fast_loop(THREADS);
+        else fast_loop(kn8);
       } else {
         if (threadIdx.x == 0) atomicOr(J.status, ST_SLOW_PHASE);
         double omt[NB][2];
@@ -583,13 +590,15 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     mbar_init(&bar, 1);
     mbar_fence_init();
   }
-  __syncthreads();
-  long long clk0 = 0;
-  unsigned long long ns0 = 0;
+  // Profiling: the block's start, kept in shared memory rather than in
+  // registers live across the whole loop.
+  __shared__ long long s_clk0;
+  __shared__ unsigned long long s_ns0;
   if (a.prof_clk && threadIdx.x == 0) {
-    clk0 = clock64();
-    ns0 = global_ns();
+    s_clk0 = clock64();
+    s_ns0 = global_ns();
   }
+  __syncthreads();
   uint32_t phase = 0u;
   int buf = 0;
   for (;;) {
@@ -610,8 +619,8 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     if (!ok) break;
   }
   if (a.prof_clk && threadIdx.x == 0) {
-    atomicAdd(&a.prof_clk[0], (unsigned long long)(clock64() - clk0));
-    atomicAdd(&a.prof_clk[1], global_ns() - ns0);
+    atomicAdd(&a.prof_clk[0], (unsigned long long)(clock64() - s_clk0));
+    atomicAdd(&a.prof_clk[1], global_ns() - s_ns0);
   }
 }
 

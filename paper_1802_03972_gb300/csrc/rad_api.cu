@@ -4,6 +4,9 @@
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
+#include <stdlib.h>
+#include <stdio.h>
+#include <stdarg.h>
 
 #include <algorithm>
 #include <atomic>
@@ -66,6 +69,20 @@ cudaError_t dmalloc(T** p, size_t count) {
 
 namespace radimpl {
 
+void rad_log(int level, const char* fmt, ...) {
+  static const int threshold = [] {
+    const char* v = getenv("RAD_LOG");
+    return v ? atoi(v) : 0;
+  }();
+  if (level > threshold) return;
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  fprintf(stderr, "[rad] %s\n", buf);
+}
+
 int current_device() {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -85,6 +102,8 @@ rad_status fail(rad_ctx* c, rad_status s) {
 
 rad_status cuda_check(rad_ctx* c, cudaError_t e) {
   if (e == cudaSuccess) return RAD_OK;
+  rad_log(1, "CUDA error %d (%s)%s", (int)e, cudaGetErrorString(e),
+          e == cudaErrorMemoryAllocation ? "" : "; the context is now failed");
   return fail(c, e == cudaErrorMemoryAllocation ? RAD_ENOMEM : RAD_ECUDA);
 }
 

@@ -123,6 +123,14 @@ int accumulate_blocks_per_sm(int variant);
 constexpr int kMaxDevices = 64;
 // The calling thread's current device, or -1 (rad_api.cu).
 int current_device();
+// Diagnostics to stderr when the environment variable RAD_LOG is set to a
+// level >= `level` (1: errors and decisions, 2: also per-job events), printf
+// style, one line per call (rad_api.cu).
+void rad_log(int level, const char* fmt, ...)
+#if defined(__GNUC__)
+    __attribute__((format(printf, 2, 3)))
+#endif
+    ;
 size_t accumulate_smem_bytes(int variant);
 cudaError_t launch_readout(const float* state, int mixed, const double* state64, int n_omega,
                            int n_bins, const double* omega, const double* dirs, rad_ff ff,

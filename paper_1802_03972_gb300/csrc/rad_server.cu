@@ -177,6 +177,8 @@ void rad_server::loop() {
       st.active++;
       st.waiting = (int32_t)waiting.size();
       st.admitted++;
+      rad_log(2, "server: job %lld admitted (%zu bytes, %d active)", (long long)j.id, j.footprint,
+              st.active);
       const rad_status s = admit_locked(j);
       if (s != RAD_OK) {
         j.err = s;
@@ -268,6 +270,9 @@ void rad_server::loop() {
       j->t_ready = Clock::now();
       j->state = (j->err == RAD_OK || j->err == RAD_EDATA) ? JobState::Done : JobState::Failed;
       st.completed++;
+      rad_log(2, "server: job %lld %s after %.3f s", (long long)j->id,
+              j->state == JobState::Done ? "done" : "failed",
+              std::chrono::duration<double>(j->t_ready - j->t_submit).count());
       release_job_locked(*j);
     }
     cv_done.notify_all();

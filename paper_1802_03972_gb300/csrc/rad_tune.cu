@@ -171,6 +171,9 @@ extern "C" rad_status rad_tune(rad_ctx* c, int64_t n) {
   if (st == RAD_OK) st = rad_state_import(c, saved, blob);
   if (st == RAD_OK) {
     rad_sync(c);  // clears status bits raised by the synthetic data, if any
+    rad_log(1, "tune: %d omega x %d directions, n ~ %lld: variant %d, omega tile %d, chunk %d (%.3f ms per trial)",
+            c->n_omega, c->n_dir, (long long)n, best.variant, best.omega_tile, best.chunk,
+            best_ms / 2.0);
     std::lock_guard<std::mutex> lk(g_mu);
     store_cache_locked(key, best);
   }

@@ -173,3 +173,31 @@ def test_server_rejects_job_larger_than_budget():
     with pytest.raises(rad.RadError):
         srv.submit(inputs.omega_log(1e14, 1e20, 1024), inputs.dirs_grid(0.01, 32, 32), max_particles=10 ** 6)
     srv.close()
+
+
+def test_rad_log_reports_decisions_and_job_events():
+    """RAD_LOG=2: the tuner's choice and each served job's admission and completion
+    are printed to stderr (the level is read once per process, hence a subprocess)."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "from paper_1802_03972_gb300 import rad, inputs\n"
+        "wl = inputs.lwfa_bunch(n_particles=300, n_omega=64, n_side=2, seed=5)\n"
+        "ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)\n"
+        "ctx.tune(wl.n_particles)\n"
+        "srv = rad.Server(hbm_budget=1 << 30, max_slots=1)\n"
+        "j = srv.submit(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width, max_particles=wl.n_particles)\n"
+        "st = wl.step(0)\n"
+        "while srv.feed(j, rad.make_step(st.n, st.r, st.beta, st.beta_dot, st.w, st.t, st.dt)) != rad.RAD_OK:\n"
+        "    pass\n"
+        "srv.finish(j)\n"
+        "srv.result(j, wl.dirs.shape[0], wl.omega.shape[0], timeout=60)\n"
+        "srv.close()\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RAD_LOG="2", PYTHONPATH=root)
+    p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr[-2000:]
+    err = p.stderr
+    assert "[rad] tune: 64 omega x 4 directions" in err, err[-2000:]
+    assert "admitted" in err and "done after" in err, err[-2000:]
