@@ -252,11 +252,14 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
     if (threadIdx.x == 0 && it + 1 < n_kt) issue_tile(J, kt + g.KT, g.KT, raw, bar);
     const float4* rc = rec + my_dl * REC;
     if (!(flags & 1)) {
+      // kend particles at a record stride of nt; a full tile of one direction
+      // instantiates it with both known at compile time.
+      auto fast_loop = [&](const int kend, const int nt) {
 #pragma unroll UNROLL
-      for (int kk = 0; kk < kn; ++kk) {
-        const float4 r0 = rc[kk * g.NT * REC + 0];
-        const float4 r1 = rc[kk * g.NT * REC + 1];
-        const float4 r2 = rc[kk * g.NT * REC + 2];
+      for (int kk = 0; kk < kend; ++kk) {
+        const float4 r0 = rc[kk * nt * REC + 0];
+        const float4 r1 = rc[kk * nt * REC + 1];
+        const float4 r2 = rc[kk * nt * REC + 2];
         const float2 th = make_float2(r0.x, r0.y), tl = make_float2(r0.z, r0.w);
         const float2 aw1 = make_float2(r1.x, r1.y), aw2 = make_float2(r1.z, r1.w);
         const float2 av1 = make_float2(r2.x, r2.y), av2 = make_float2(r2.z, r2.w);
@@ -274,7 +277,7 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
           acc1[p][6] = __ffma2_rn(av2, cc, acc1[p][6]);
           acc1[p][7] = __ffma2_rn(av2, ss, acc1[p][7]);
           if (LIT) {
-            const float4 r3 = rc[kk * g.NT * REC + REC - 1];
+            const float4 r3 = rc[kk * nt * REC + REC - 1];
             const float2 g2 = __ffma2_rn(make_float2(r3.x, r3.y), f2[p], kOne);
             const float2 gg = make_float2(sqrt_approx(g2.x), sqrt_approx(g2.y));
             const float2 pv1 = __fmul2_rn(av1, gg), pv2 = __fmul2_rn(av2, gg);
@@ -285,6 +288,9 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
           }
         }
       }
+      };
+      if (g.NT == 1 && kn == THREADS) fast_loop(THREADS, 1);
+      else fast_loop(kn, g.NT);
     } else {
       // Wide path: some |dtau| exceed the fast range in this tile; the phase of
       // every update is formed in FP64.
