@@ -282,10 +282,13 @@ rad_status rad_server_create(size_t hbm_budget, int32_t max_slots, void* stream,
  *     amplitude updates (particles x bins), at least one job;
  *   RAD_SERVE_LEAST_SERVED (default, round_updates = 2e10): the same in order of
  *     the updates each job has had so far (new and small jobs first; ties in
- *     arrival order).
- * round_updates >= 1 for the last two (ignored for RAD_SERVE_ALL).  Takes effect
+ *     arrival order);
+ *   RAD_SERVE_LEAST_SERVED_AGED: as least served, with each job's updates reduced
+ *     by its time since submission times one round's updates per 12 ms, so that
+ *     large jobs that have waited long are not passed over indefinitely.
+ * round_updates >= 1 for all but RAD_SERVE_ALL, which ignores it.  Takes effect
  * from the next round.  RAD_EINVAL for an unknown policy or round_updates < 1. */
-enum { RAD_SERVE_ALL = 0, RAD_SERVE_OLDEST = 1, RAD_SERVE_LEAST_SERVED = 2 };
+enum { RAD_SERVE_ALL = 0, RAD_SERVE_OLDEST = 1, RAD_SERVE_LEAST_SERVED = 2, RAD_SERVE_LEAST_SERVED_AGED = 3 };
 rad_status rad_server_set_policy(rad_server* s, int32_t policy, int64_t round_updates);
 /* Copies the grids; the job waits until it can be admitted. RAD_EINVAL if it
  * could never fit the budget. */

@@ -197,6 +197,22 @@ void rad_server::loop() {
     if (policy == RAD_SERVE_LEAST_SERVED)
       std::stable_sort(ready.begin(), ready.end(),
                        [](const Job* a, const Job* b) { return a->served < b->served; });
+    if (policy == RAD_SERVE_LEAST_SERVED_AGED) {
+      // Attained service minus a credit for the time since submission, at one
+      // round's updates per 12 ms (about the GPU's rate): a job that has waited
+      // t seconds competes like one that has had that much less work.
+      const Clock::time_point now = Clock::now();
+      const double credit = (double)round_updates / 0.012;
+      std::vector<std::pair<double, Job*>> keyed;
+      keyed.reserve(ready.size());
+      for (Job* jp : ready)
+        keyed.emplace_back((double)jp->served -
+                               credit * std::chrono::duration<double>(now - jp->t_submit).count(),
+                           jp);
+      std::stable_sort(keyed.begin(), keyed.end(),
+                       [](const auto& a, const auto& b) { return a.first < b.first; });
+      for (size_t i = 0; i < keyed.size(); ++i) ready[i] = keyed[i].second;
+    }
     std::vector<rad_ctx*> ctxs;
     std::vector<rad_step> steps;
     std::vector<Job*> in_round;
@@ -317,7 +333,7 @@ rad_status rad_server_create(size_t hbm_budget, int32_t max_slots, void* stream,
 }
 
 rad_status rad_server_set_policy(rad_server* s, int32_t policy, int64_t round_updates) {
-  if (!s || policy < RAD_SERVE_ALL || policy > RAD_SERVE_LEAST_SERVED) return RAD_EINVAL;
+  if (!s || policy < RAD_SERVE_ALL || policy > RAD_SERVE_LEAST_SERVED_AGED) return RAD_EINVAL;
   if (policy != RAD_SERVE_ALL && round_updates < 1) return RAD_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
   s->policy = policy;

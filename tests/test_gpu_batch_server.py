@@ -120,7 +120,7 @@ def test_tune_keeps_parity():
     assert row_error(ctx.spectrum()[2], ref["tot"]) <= TOL_TOTAL
 
 
-@pytest.mark.parametrize("policy", [(0, 0), (1, 1), (2, 1_000_000)])
+@pytest.mark.parametrize("policy", [(0, 0), (1, 1), (2, 1_000_000), (3, 1_000_000)])
 def test_server_results_equal_alone_and_in_the_mix(policy):
     """Jobs submitted at different times, steps fed incrementally, one slot fewer
     than jobs (admission waits); each result equals the standalone run, under
@@ -161,7 +161,7 @@ def test_server_results_equal_alone_and_in_the_mix(policy):
 
 def test_server_policy_arguments():
     srv = rad.Server(hbm_budget=1 << 30, max_slots=2)
-    for bad in ((3, 10), (-1, 10), (1, 0), (2, -5)):
+    for bad in ((4, 10), (-1, 10), (1, 0), (2, -5), (3, 0)):
         with pytest.raises(rad.RadError):
             srv.set_policy(*bad)
     srv.set_policy(rad.SERVE_ALL, 0)
