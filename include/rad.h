@@ -164,6 +164,21 @@ rad_status rad_push_flush(rad_ctx* ctx);
  * creation shape.  RAD_ESTATE for other contexts.  Synchronises the stream. */
 rad_status rad_spectrum_literal(rad_ctx* ctx, double* literal);
 
+/* rad_spectrum_species - spectra of a particle population made of several
+ * species (particle classes), each accumulated in its own context with its own
+ * macro-particle shape ffs[s] (Sec. 3.2 per species, optionally RAD_FF_3D):
+ *   coherent   = K0 |sum_s f_s U_s|^2   (amplitudes of all species add first),
+ *   incoherent = K0 sum_s (1 - f_s^2) |V_s|^2,   total = their sum.
+ * ctxs: n_species distinct contexts (1 <= n_species <= 16) created with the
+ * same frequencies, directions and precision; ffs: their shapes.  Outputs as in
+ * rad_spectrum ([n_dir][n_omega] doubles, host or device, NULL to skip), written
+ * on the first context's stream.  Synchronises every context.  Errors:
+ * RAD_EINVAL (grids or precisions differ, a context repeated, a bad shape),
+ * RAD_ESTATE, RAD_ECUDA; RAD_EDATA once, after writing the spectra, when a
+ * species saw invalid particles. */
+rad_status rad_spectrum_species(rad_ctx* const* ctxs, const rad_ff* ffs, int32_t n_species,
+                                double* coherent, double* incoherent, double* total);
+
 /* rad_sync - wait for the context's queued work; report RAD_EDATA / errors. */
 rad_status rad_sync(rad_ctx* ctx);
 

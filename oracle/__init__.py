@@ -186,3 +186,29 @@ def accumulate_particles(bin_omega, bin_dir, r, beta, beta_dot, t, dt, a=None) -
 
 def complex_particles(a: np.ndarray) -> np.ndarray:
     return a[..., 0::2] + 1j * a[..., 1::2]
+
+
+def species_spectra(accs, ffs) -> dict:
+    """Spectra of a population made of several species (Sec. 3.2 applied per
+    particle class): accs[s] holds species s's sums on a common bin list and
+    ffs[s] = (kind, width[, flags]) its macro-particle shape.  The coherent
+    amplitudes of all species add before the square; the incoherent part is a
+    sum over species:
+        coh = K0 |sum_s f_s U_s|^2,  inc = K0 sum_s (1 - f_s^2) |V_s|^2."""
+    accs = list(accs)
+    a0 = accs[0]
+    nb = a0.n_bins
+    u = np.zeros((nb, 3), dtype=complex)
+    inc = np.zeros(nb)
+    for acc, ff in zip(accs, ffs, strict=True):
+        assert np.array_equal(acc.bin_omega, a0.bin_omega) and np.array_equal(acc.bin_dir, a0.bin_dir)
+        kind, width = int(ff[0]), float(ff[1])
+        flags = int(ff[2]) if len(ff) > 2 else 0
+        f = np.array([form_factor_dir(kind, flags, width, om, n)
+                      for om, n in zip(acc.bin_omega, acc.bin_dir)])
+        amp = acc.amplitudes()
+        u += f[:, None] * amp["U"]
+        inc += (1.0 - f ** 2) * np.sum(np.abs(amp["V"]) ** 2, axis=1)
+    coh = k0() * np.sum(np.abs(u) ** 2, axis=1)
+    inc = k0() * inc
+    return {"coh": coh, "inc": inc, "tot": coh + inc}

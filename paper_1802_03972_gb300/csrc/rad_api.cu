@@ -363,6 +363,16 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
   }
   rad_ctx* c = new (std::nothrow) rad_ctx();
   if (!c) return RAD_ENOMEM;
+  {  // FNV-1a over the grids' bytes: contexts read out together must share them
+    uint64_t h = 1469598103934665603ULL;
+    auto mix = [&h](const void* p, size_t n) {
+      const unsigned char* b = static_cast<const unsigned char*>(p);
+      for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ULL;
+    };
+    mix(omega, sizeof(double) * (size_t)n_omega);
+    mix(nd.data(), sizeof(double) * nd.size());
+    c->grid_hash = h;
+  }
   c->n_omega = n_omega;
   c->n_dir = n_dir;
   c->n_bins = n_omega * n_dir;
@@ -580,6 +590,63 @@ rad_status rad_spectrum_ff(rad_ctx* c, rad_ff ff, double* coh, double* inc, doub
     if (s != RAD_OK) return s;
   }
   return check_status_word(c);
+}
+
+rad_status rad_spectrum_species(rad_ctx* const* ctxs, const rad_ff* ffs, int32_t n_species,
+                                double* coh, double* inc, double* tot) {
+  radimpl::TraceRange trace("rad_spectrum_species");
+  if (!ctxs || !ffs || n_species < 1 || n_species > kMaxSpecies) return RAD_EINVAL;
+  rad_ctx* c0 = ctxs[0];
+  if (!c0) return RAD_EINVAL;
+  SpeciesArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n_species = n_species;
+  a.mixed = c0->prec == RAD_PREC_MIXED;
+  for (int i = 0; i < n_species; ++i) {
+    rad_ctx* c = ctxs[i];
+    const rad_ff& ff = ffs[i];
+    if (!c) return RAD_EINVAL;
+    if (c->failed) return RAD_ESTATE;
+    if (c->n_omega != c0->n_omega || c->n_dir != c0->n_dir || c->grid_hash != c0->grid_hash ||
+        c->prec != c0->prec)
+      return fail(c0, RAD_EINVAL);
+    if (ff.kind < RAD_FF_POINT || ff.kind > RAD_FF_GAUSS || !(ff.width >= 0.0) ||
+        !isfinite(ff.width) || (ff.flags & ~(RAD_FF_3D | RAD_FF_LITERAL)) != 0)
+      return fail(c0, RAD_EINVAL);
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(c0, RAD_EINVAL);  // a species counted twice
+    a.state[i] = c->d_state;
+    a.state64[i] = c->d_state64;
+    a.kind[i] = ff.kind;
+    a.flags[i] = ff.flags;
+    a.width[i] = ff.width;
+  }
+  // Every species' queued work must be complete before its state is read; a
+  // species that saw invalid particles is reported after the spectra are written.
+  rad_status data = RAD_OK;
+  for (int i = 0; i < n_species; ++i) {
+    const rad_status s = check_status_word(ctxs[i]);
+    if (s == RAD_EDATA) data = RAD_EDATA;
+    else if (s != RAD_OK) return s;
+  }
+  double* outs[3] = {coh, inc, tot};
+  double* dev_out[3];
+  bool host[3];
+  for (int i = 0; i < 3; ++i) {
+    host[i] = outs[i] && !is_device_ptr(outs[i]);
+    dev_out[i] = outs[i] ? (host[i] ? c0->d_spec + (size_t)i * c0->n_bins : outs[i]) : nullptr;
+  }
+  rad_status s = cuda_check(c0, launch_readout_species(a, c0->n_omega, c0->n_bins, c0->d_omega,
+                                                       c0->d_dirs, dev_out[0], dev_out[1],
+                                                       dev_out[2], c0->stream));
+  for (int i = 0; s == RAD_OK && i < 3; ++i) {
+    if (!host[i]) continue;
+    s = cuda_check(c0, cudaMemcpyAsync(outs[i], dev_out[i], sizeof(double) * c0->n_bins,
+                                       cudaMemcpyDeviceToHost, c0->stream));
+  }
+  if (s == RAD_OK) s = cuda_check(c0, cudaStreamSynchronize(c0->stream));
+  if (s != RAD_OK) return s;
+  return data;
 }
 
 rad_status rad_spectrum(rad_ctx* c, double* coh, double* inc, double* tot) {

@@ -49,6 +49,7 @@ struct rad_ctx {
   size_t prof_used = 0;
   unsigned long long* d_prof_clk = nullptr;  // [2] cycles, ns of the accumulate CTAs
   long long generation = 0;      // bumped whenever d_js changes
+  uint64_t grid_hash = 0;        // FNV-1a of the frequencies and unit directions
   rad_status last_err = RAD_OK;
   bool failed = false;
 };

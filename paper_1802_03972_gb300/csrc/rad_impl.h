@@ -132,6 +132,20 @@ void rad_log(int level, const char* fmt, ...)
 #endif
     ;
 size_t accumulate_smem_bytes(int variant);
+// Readout of several species accumulated in separate contexts on one grid:
+// coherent K0 |sum_s f_s U_s|^2, incoherent K0 sum_s (1 - f_s^2) |V_s|^2.
+constexpr int kMaxSpecies = 16;
+struct SpeciesArgs {
+  int n_species;
+  int mixed;                         // 1: FP32 state with compensation, 0: FP64 state
+  const float* state[kMaxSpecies];   // mixed
+  const double* state64[kMaxSpecies];
+  int kind[kMaxSpecies], flags[kMaxSpecies];
+  double width[kMaxSpecies];
+};
+cudaError_t launch_readout_species(const SpeciesArgs& a, int n_omega, int n_bins,
+                                   const double* omega, const double* dirs, double* coh,
+                                   double* inc, double* tot, cudaStream_t s);
 cudaError_t launch_readout(const float* state, int mixed, const double* state64, int n_omega,
                            int n_bins, const double* omega, const double* dirs, rad_ff ff,
                            double* coh, double* inc, double* tot, cudaStream_t s);

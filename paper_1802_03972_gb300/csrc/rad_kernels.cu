@@ -141,6 +141,41 @@ __global__ void readout_kernel(const float* __restrict__ state, const double* __
   if (tot) tot[bin] = ic + ii;
 }
 
+__global__ void readout_species_kernel(SpeciesArgs a, int n_omega, int n_bins,
+                                       const double* __restrict__ omega,
+                                       const double* __restrict__ dirs, double k0, double* coh,
+                                       double* inc, double* tot) {
+  const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bin >= n_bins) return;
+  const int d = bin / n_omega;
+  const double om = omega[bin - d * n_omega];
+  const int nu = a.mixed ? 4 : 6;  // real components of U (and of V)
+  double u[6] = {0, 0, 0, 0, 0, 0};
+  double ii = 0.0;
+  for (int s = 0; s < a.n_species; ++s) {
+    const double f = form_factor_dir(a.kind[s], a.flags[s], a.width[s], om, dirs + 3 * d);
+    double v2 = 0.0;
+    for (int c = 0; c < 2 * nu; ++c) {
+      double x;
+      if (a.mixed)
+        x = (double)a.state[s][(size_t)c * n_bins + bin] -
+            (double)a.state[s][(size_t)(kComps + c) * n_bins + bin];
+      else
+        x = a.state64[s][(size_t)c * n_bins + bin];
+      if (c < nu) u[c] += f * x;  // amplitudes add across species before |.|^2
+      else v2 += x * x;
+    }
+    ii += (1.0 - f * f) * v2;
+  }
+  double u2 = 0.0;
+  for (int c = 0; c < nu; ++c) u2 += u[c] * u[c];
+  const double ic = k0 * u2;
+  ii *= k0;
+  if (coh) coh[bin] = ic;
+  if (inc) inc[bin] = ii;
+  if (tot) tot[bin] = ic + ii;
+}
+
 // ----------------------------------------------------------- plain FP64 K5
 // One thread per (direction, frequency) bin; every particle's amplitude and
 // phase in FP64 with the library sincos, summed in FP64 (Eq. 1, Eq. 13).
@@ -255,6 +290,16 @@ cudaError_t launch_readout(const float* state, int mixed, const double* state64,
   readout_kernel<<<(n_bins + 255) / 256, 256, 0, s>>>(state, state64, mixed, n_omega, n_bins,
                                                        omega, dirs, ff.kind, ff.flags, ff.width,
                                                        k0, coh, inc, tot);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_readout_species(const SpeciesArgs& a, int n_omega, int n_bins,
+                                   const double* omega, const double* dirs, double* coh,
+                                   double* inc, double* tot, cudaStream_t s) {
+  const double k0 = kQe * kQe / (16.0 * kPi * kPi * kPi * kEps0 * kC);
+  readout_species_kernel<<<(n_bins + 255) / 256, 256, 0, s>>>(a, n_omega, n_bins, omega, dirs, k0,
+                                                              coh, inc, tot);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -25,7 +25,8 @@ STATUS_NAMES = ["RAD_OK", "RAD_EINVAL", "RAD_ENOMEM", "RAD_ECUDA", "RAD_EDATA", 
 
 # Every symbol include/rad.h and include/rad_probe.h declare.
 EXPORTS = [
-    "rad_create", "rad_accumulate", "rad_spectrum", "rad_spectrum_ff", "rad_sync", "rad_reset",
+    "rad_create", "rad_accumulate", "rad_spectrum", "rad_spectrum_ff", "rad_spectrum_species",
+    "rad_sync", "rad_reset",
     "rad_destroy", "rad_state_size", "rad_state_export", "rad_state_import", "rad_state_merge",
     "rad_get_tile", "rad_set_tile", "rad_tune", "rad_batch_create", "rad_batch_accumulate",
     "rad_batch_sync", "rad_batch_destroy", "rad_server_create", "rad_server_set_policy", "rad_job_submit", "rad_job_feed",
@@ -96,6 +97,7 @@ def load(path: str = LIB_PATH):
         "rad_accumulate": (st, [vp, i64, vp, vp, vp, vp, dbl, dbl]),
         "rad_spectrum": (st, [vp, vp, vp, vp]),
         "rad_spectrum_ff": (st, [vp, rad_ff, vp, vp, vp]),
+        "rad_spectrum_species": (st, [vp, vp, i32, vp, vp, vp]),
         "rad_sync": (st, [vp]),
         "rad_reset": (st, [vp]),
         "rad_destroy": (None, [vp]),
@@ -199,6 +201,26 @@ def selftest_wait(limit_ns: int) -> tuple:
     _check(load().rad_selftest_wait(int(limit_ns), ctypes.byref(flag), ctypes.byref(waited)),
            "rad_selftest_wait")
     return bool(flag.value), waited.value
+
+
+def spectrum_species(contexts, ffs, out=None, accept_edata: bool = False):
+    """rad_spectrum_species: (coherent, incoherent, total) of several species, each a
+    Context on the same grid with its own shape ffs[s] = (kind, width[, flags]);
+    the coherent amplitudes of all species add before |.|^2."""
+    contexts = list(contexts)
+    n = len(contexts)
+    if n != len(ffs):
+        raise ValueError("one shape per species")
+    c0 = contexts[0]
+    if out is None:
+        out = tuple(np.zeros((c0.n_dir, c0.n_omega)) for _ in range(3))
+    handles = (ctypes.c_void_p * n)(*[c.handle.value for c in contexts])
+    shapes = (rad_ff * n)(*[rad_ff(int(f[0]), int(f[2]) if len(f) > 2 else 0, float(f[1])) for f in ffs])
+    st = load().rad_spectrum_species(ctypes.addressof(handles), ctypes.addressof(shapes), n,
+                                     *[_ptr(o) for o in out])
+    if not (accept_edata and st == RAD_EDATA):
+        _check(st, "rad_spectrum_species")
+    return out
 
 
 def probe_tensor() -> np.ndarray:

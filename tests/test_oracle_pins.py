@@ -496,3 +496,84 @@ def test_brute_force_3d_box_offsets_oblique_direction(shape):
     mean, se = vals.mean(), vals.std(ddof=1) / math.sqrt(R)
     assert abs(mean - want) <= 5 * se, (mean / want, se / want)
     assert abs(mean - want_1d) > 5 * se  # the direction dependence is resolved
+
+
+def test_species_single_and_split_population():
+    """One species reads out exactly as the single-shape readout.  A population
+    split into two species of the same shape has the coherent part of one
+    accumulator fed all particles (the species' amplitudes add before |.|^2,
+    Eq. 13 with one f for all macro-particles), and an incoherent part that is
+    the sum of the species' own incoherent parts (Eq. 12 per species: no
+    cross-species terms)."""
+    rng = np.random.default_rng(23)
+    r, b, bd, w = _random_bunch(rng, 10)
+    bo, bdir = oracle.grid_bins([2e14, 3e15, 5e16], [[0, 0, 1.0], [0.3, -0.2, math.sqrt(0.87)]])
+    for ff in ((oracle.FF_TSC, 0.4e-6), (oracle.FF_CIC, 0.3e-6, oracle.FF_3D)):
+        flags = ff[2] if len(ff) > 2 else 0
+        whole = oracle.Accumulator(bo, bdir, ff[0], ff[1], flags)
+        parts = [oracle.Accumulator(bo, bdir, ff[0], ff[1], flags) for _ in range(2)]
+        for t in np.arange(6) * 1e-16:
+            whole.accumulate(r, b, bd, w, t, 1e-16)
+            for acc, sl in zip(parts, (slice(0, 4), slice(4, 10))):
+                acc.accumulate(r[:, sl], b[:, sl], bd[:, sl], w[sl], t, 1e-16)
+        want = whole.spectra()
+        one = oracle.species_spectra([whole], [ff])
+        two = oracle.species_spectra(parts, [ff, ff])
+        for k in ("coh", "inc", "tot"):
+            np.testing.assert_allclose(one[k], want[k], rtol=1e-13, atol=0)
+        np.testing.assert_allclose(two["coh"], want["coh"], rtol=1e-12, atol=1e-300)
+        inc_sum = parts[0].spectra()["inc"] + parts[1].spectra()["inc"]
+        np.testing.assert_allclose(two["inc"], inc_sum, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(two["tot"], two["coh"] + two["inc"], rtol=1e-15, atol=0)
+        assert np.all(want["inc"] > 0) and np.any(want["coh"] > 0)
+
+
+def test_brute_force_two_species_of_different_shapes():
+    """Sec. 3.2 per particle class: two macro-particles of different shapes (a
+    CIC species and a Gaussian species) replaced by w electrons at offsets drawn
+    from each one's own shape.  The mean of |sum|^2 over realisations equals
+    K0 [|f_A w_A a_A + f_B w_B a_B|^2 + sum_s (1 - f_s^2) w_s |a_s|^2]: the
+    species readout, whose coherent cross term carries f_A f_B."""
+    rng = np.random.default_rng(29)
+    traj, times, dt = _short_helix(n_steps=12)
+    n = np.array([0.0, 0.0, 1.0])
+    delta, sigma = 0.12e-6, 0.08e-6
+    om = 1.0 * 2 * C / delta   # CIC: f^2 = sinc^2(1) ~ 0.71
+    ffs = [(oracle.FF_CIC, delta), (oracle.FF_GAUSS, sigma)]
+    f = [oracle.form_factor(k, wd, om)[0] for k, wd in ffs]
+    assert 0.1 < f[0] ** 2 < 0.9 and 0.1 < f[1] ** 2 < 0.9
+    w_list = [5, 7]
+    centers = [np.zeros(3), np.array([0.0, 0.0, 0.29e-6])]
+    accs = [oracle.Accumulator([om], [n], k, wd) for k, wd in ffs]
+    for t in times:
+        r, b, bd = traj(t)
+        for s in range(2):
+            accs[s].accumulate((r + centers[s])[:, None], b[:, None], bd[:, None],
+                               np.array([float(w_list[s])]), t, dt)
+    want = oracle.species_spectra(accs, ffs)["tot"][0]
+    R = 1500
+
+    def draw(s, m):
+        if s == 1:
+            return rng.normal(0.0, sigma, size=(3, m))
+        return np.stack([np.zeros(m), np.zeros(m), rng.uniform(-0.5, 0.5, m) * delta])
+
+    owner = np.repeat(np.arange(2), w_list)
+    ne = owner.size
+    offs = [np.concatenate([draw(s, w_list[s]) for s in range(2)], axis=1) for _ in range(R)]
+    el = None
+    for t in times:
+        r, b, bd = traj(t)
+        rr = np.concatenate([np.stack([r + centers[o] for o in owner], 1) + off for off in offs], 1)
+        m = rr.shape[1]
+        el = oracle.accumulate_particles([om], [n], rr, np.repeat(b[:, None], m, 1),
+                                         np.repeat(bd[:, None], m, 1), t, dt, el)
+    z = oracle.complex_particles(el)[:, 0, :].reshape(R, ne, 3).sum(axis=1)
+    vals = oracle.k0() * np.sum(np.abs(z) ** 2, axis=1)
+    mean, se = vals.mean(), vals.std(ddof=1) / math.sqrt(R)
+    assert abs(mean - want) <= 5 * se, (mean / want, se / want)
+    # the pin discriminates: reading both species with one shape, or dropping the
+    # coherent cross term between species, misses by many sigma
+    wrong = [oracle.species_spectra(accs, [ff, ff])["tot"][0] for ff in ffs]
+    wrong.append(sum(a.spectra()["tot"][0] for a in accs))
+    assert all(abs(mean - x) > 5 * se for x in wrong), [(x / want) for x in wrong]
