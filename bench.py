@@ -222,8 +222,9 @@ def reference_arm(args, wl):
 def modes_leg(wl, ring_dev, steps_host, upd: int, n_steps: int = 20):
     """Throughput of the other accumulation modes on the headline workload:
     the paper's literal sum (FF_LITERAL), in-situ coupling (push_step: beta_dot
-    differenced on the device) and the readout with the direction-dependent 3-D
-    box form factor, each timed with CUDA events on the current stream."""
+    differenced on the device), the readout with the direction-dependent 3-D
+    box form factor and the readout of two species with different shapes, each
+    timed with CUDA events on the current stream."""
     import torch
 
     from paper_1802_03972_gb300 import rad
@@ -242,7 +243,6 @@ def modes_leg(wl, ring_dev, steps_host, upd: int, n_steps: int = 20):
     torch.cuda.synchronize()
     out["literal_sum"] = {"value": n_steps * upd / (a.elapsed_time(b) / 1e3), "unit": UNIT,
                           "steps": n_steps, "tile": list(lit.get_tile())}
-    lit.close()
     push = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
     a, b = ev(), ev()
     a.record()
@@ -267,8 +267,18 @@ def modes_leg(wl, ring_dev, steps_host, upd: int, n_steps: int = 20):
         b.record()
         torch.cuda.synchronize()
         times[name] = a.elapsed_time(b) / 10
+    species = ([push, lit], [(rad.FF_GAUSS, 0.1e-6), (rad.FF_CIC, 0.1e-6, rad.FF_3D)])
+    rad.spectrum_species(*species, out=bufs)
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(10):
+        rad.spectrum_species(*species, out=bufs)
+    b.record()
+    torch.cuda.synchronize()
+    times["readout_2_species_ms"] = a.elapsed_time(b) / 10
     out["readout"] = dict(times, bins=int(wl.dirs.shape[0] * wl.omega.shape[0]))
     push.close()
+    lit.close()
     return out
 
 
