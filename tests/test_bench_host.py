@@ -3,6 +3,7 @@ latencies it reports beside the serving legs, and the lookup of the committed
 DRAM-traffic capture."""
 import importlib.util
 import json
+import math
 import os
 
 import pytest
@@ -50,3 +51,14 @@ def test_committed_traffic_capture_is_well_formed(bench):
         assert len(c["kernel_sha"]) == 16 and len(c["tile"]) == 3
         assert c["dram_bytes_per_launch"] == pytest.approx(c["dram_bytes_read"] + c["dram_bytes_write"])
         assert "--clock-control none" in c["command"]
+
+
+def test_error_stats_by_hand(bench):
+    ref = [[1.0, 2.0, 1e-9, 0.0], [0.0, 0.0, 0.0, 0.0]]
+    got = [[1.0 + 1e-6, 2.0, 5e-9, 0.0], [0.0, 0.0, 0.0, 0.0]]
+    r = bench.error_stats(got, ref)
+    # row 0: ||(1e-6, 0, 4e-9, 0)|| / ||(1, 2, 1e-9, 0)||; the all-zero row counts as exact
+    assert r["row"] == pytest.approx(math.hypot(1e-6, 4e-9) / math.sqrt(5.0 + 1e-18), rel=1e-9)
+    # bins kept: >= 1e-6 of the row maximum, so 1e-9 and 0 are left out
+    assert r["bins"] == 2 and r["bin_max"] == pytest.approx(1e-6, rel=1e-9)
+    assert bench.error_stats([[0.0, 1.0]], [[0.0, 0.0]])["row"] == math.inf
