@@ -617,8 +617,10 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     const JobStatic& J = a.js[j];
     const JobCall K = a.use_inline ? a.inline_call : a.jc[j];
     const long long local = item - K.item_begin;
-    const int tile = (int)(local % J.n_tiles);
-    const int chunk = (int)(local / J.n_tiles);
+    // Tile-major order: the chunks of one tile run close together in time, so
+    // their partial sums are still in L2 when the tile's last arrival reads them.
+    const int chunk = (int)(local % K.n_chunks);
+    const int tile = (int)(local / K.n_chunks);
     bool ok;
     if constexpr (TC) ok = process_item_tc<THREADS, PASSES>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
     else ok = process_item_fma<THREADS, W, 2, LIT>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
