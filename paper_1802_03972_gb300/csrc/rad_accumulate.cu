@@ -103,6 +103,37 @@ __device__ __forceinline__ bool last_arrival(const JobStatic& J, const JobCall& 
   return *s_flag != 0;
 }
 
+// Drops one 128-byte L2 line without writing it back (its contents become
+// undefined; the line must not be read again before it is rewritten).
+__device__ __forceinline__ void discard_l2_line(const void* p) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
+// The partial sums of a tile are dead once the last arrival has added them up,
+// and every call rewrites each slot before reading it.  Dropping their L2
+// lines saves the write-back to DRAM.  Arrays: n_arrays consecutive [n_bins]
+// float arrays from base; only whole lines inside the tile's bin range of each
+// direction are dropped, so the neighbouring tiles' partials are untouched.
+template <int THREADS>
+__device__ __forceinline__ void discard_tile_partials(const float* base, long long n_arrays,
+                                                      const JobStatic& J, const TileGeom& g) {
+  // Four arrays per warp, eight lanes per array: a 256-bin row is 8 lines.
+  const int sub = threadIdx.x >> 3, l8 = threadIdx.x & 7;
+  const int n_om = J.n_omega, o1 = min(g.o0 + g.WT, n_om);
+  for (long long arr = sub; arr < n_arrays; arr += THREADS / 8) {
+    for (int dl = 0; dl < g.NT; ++dl) {
+      const int d = g.d0 + dl;
+      if (d >= J.n_dir) break;
+      const float* rp = base + (size_t)arr * J.n_bins + (size_t)d * n_om;
+      const uintptr_t a0 = reinterpret_cast<uintptr_t>(rp + g.o0);
+      const uintptr_t a1 = reinterpret_cast<uintptr_t>(rp + o1);
+      for (uintptr_t line = ((a0 + 127) & ~(uintptr_t)127) + (uintptr_t)l8 * 128; line + 128 <= a1;
+           line += 8 * 128)
+        discard_l2_line(reinterpret_cast<const void*>(line));
+    }
+  }
+}
+
 // Last arrival: for every bin of the tile, add the chunks' partials in chunk
 // order, rotate by e^{i omega tau_ref(n)} and add into the state (Kahan).
 template <int THREADS>
@@ -153,6 +184,9 @@ __device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall&
       }
     }
   }
+  __syncthreads();  // every thread's reads of the partials are done
+  discard_tile_partials<THREADS>(J.partials, (long long)K.n_chunks * kComps, J, g);
+  if (J.literal) discard_tile_partials<THREADS>(J.partials_p, (long long)K.n_chunks * 4, J, g);
 }
 
 __device__ __forceinline__ float sqrt_approx(float x) {
