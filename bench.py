@@ -42,7 +42,9 @@ VARIANT_NAMES = {0: "FP32 FMA, 256 threads x 2 omega, 3 CTAs/SM",
                  4: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads, 4 CTAs/SM",
                  5: "FP32 FMA, 256 threads x 2 omega, 4 CTAs/SM",
                  7: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads, 3 CTAs/SM, "
-                    "two frequency passes per staged particle tile"}
+                    "two frequency passes per staged particle tile",
+                 8: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads x 2 omega "
+                    "(64 per warp), 2 CTAs/SM"}
 KERNEL_SRC = os.path.join(ROOT, "paper_1802_03972_gb300", "csrc", "rad_accumulate.cu")
 
 

@@ -136,7 +136,9 @@ __device__ __forceinline__ void discard_tile_partials(const float* base, long lo
 
 // Last arrival: for every bin of the tile, add the chunks' partials in chunk
 // order, rotate by e^{i omega tau_ref(n)} and add into the state (Kahan).
-template <int THREADS>
+// DISCARD: then drop the partials' L2 lines (tensor-core variants; the FP32
+// variants measured slower with it and keep the write-back).
+template <int THREADS, bool DISCARD>
 __device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall& K, int tile) {
   const TileGeom g = tile_geom(J, tile, THREADS);
   const int nb = J.n_bins, n_om = J.n_omega;
@@ -184,9 +186,11 @@ __device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall&
       }
     }
   }
-  __syncthreads();  // every thread's reads of the partials are done
-  discard_tile_partials<THREADS>(J.partials, (long long)K.n_chunks * kComps, J, g);
-  if (J.literal) discard_tile_partials<THREADS>(J.partials_p, (long long)K.n_chunks * 4, J, g);
+  if constexpr (DISCARD) {
+    __syncthreads();  // every thread's reads of the partials are done
+    discard_tile_partials<THREADS>(J.partials, (long long)K.n_chunks * kComps, J, g);
+    if (J.literal) discard_tile_partials<THREADS>(J.partials_p, (long long)K.n_chunks * 4, J, g);
+  }
 }
 
 __device__ __forceinline__ float sqrt_approx(float x) {
@@ -223,14 +227,13 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
   const int s1_dl = threadIdx.x / g.KT, s1_kk = threadIdx.x - s1_dl * g.KT;
   const int s1_d = min(g.d0 + s1_dl, J.n_dir - 1);
 
-  float2 omh[NP], nomh[NP], wh[NP], wl[NP];
+  float2 omh[NP], wh[NP], wl[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     const int i0 = min(om_first + 2 * p, n_om - 1), i1 = min(om_first + 2 * p + 1, n_om - 1);
     omh[p] = make_float2(__ldg(J.om_tab + i0), __ldg(J.om_tab + i1));
-    nomh[p] = make_float2(__ldg(J.om_tab + n_om + i0), __ldg(J.om_tab + n_om + i1));
-    wh[p] = make_float2(__ldg(J.om_tab + 2 * n_om + i0), __ldg(J.om_tab + 2 * n_om + i1));
-    wl[p] = make_float2(__ldg(J.om_tab + 3 * n_om + i0), __ldg(J.om_tab + 3 * n_om + i1));
+    wh[p] = make_float2(__ldg(J.om_tab + n_om + i0), __ldg(J.om_tab + n_om + i1));
+    wl[p] = make_float2(__ldg(J.om_tab + 2 * n_om + i0), __ldg(J.om_tab + 2 * n_om + i1));
   }
   float2 f2[NP];
   if (LIT) {
@@ -299,7 +302,7 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
         const float2 av1 = make_float2(r2.x, r2.y), av2 = make_float2(r2.z, r2.w);
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
-          const float2 ph = phase2(omh[p], nomh[p], wh[p], wl[p], th, tl);
+          const float2 ph = phase2(omh[p], wh[p], wl[p], th, tl);
           const float2 cc = make_float2(cos_approx(ph.x), cos_approx(ph.y));
           const float2 ss = make_float2(sin_approx(ph.x), sin_approx(ph.y));
           acc1[p][0] = __ffma2_rn(aw1, cc, acc1[p][0]);
@@ -397,7 +400,7 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
         }
       }
   }
-  if (last_arrival<THREADS>(J, K, tile, s_flag)) tile_epilogue<THREADS>(J, K, tile);
+  if (last_arrival<THREADS>(J, K, tile, s_flag)) tile_epilogue<THREADS, false>(J, K, tile);
   return true;
 }
 
@@ -445,12 +448,13 @@ __device__ __forceinline__ void tc_block(float2 pA, float2 pB, uint32_t b0, uint
 
 // Warp layout: warp w handles direction d0 + w / (WT/32) and 32 frequencies
 // (two 16-row MMA blocks) starting at o0 + 32 (w % (WT/32)).
-template <int THREADS, int PASSES>
+template <int THREADS, int PASSES, int NB>
 __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCall& K, int tile,
                                                 int chunk, unsigned char* __restrict__ smem,
                                                 uint64_t* bar, uint32_t& phase, int* s_flag) {
-  constexpr int NB = 2;  // 16-frequency blocks per warp
-  using S = Smem<THREADS, true, false, PASSES>;
+  // NB: 16-frequency blocks per warp; GQ: second-level float4 groups per pass
+  constexpr int GQ = 2 * NB;
+  using S = Smem<THREADS, true, false, PASSES * NB / 2>;
   float* raw = reinterpret_cast<float*>(smem);
   const TileGeom g = tile_geom(J, tile, THREADS);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -467,15 +471,14 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
   const int s1_dl = threadIdx.x / g.KT, s1_kk = threadIdx.x - s1_dl * g.KT;
   const int s1_d = min(g.d0 + s1_dl, J.n_dir - 1);
 
-  float2 omh[NB], nomh[NB], wh[NB], wl[NB];
+  float2 omh[NB], wh[NB], wl[NB];
   auto load_omega = [&](int o_warp) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int i0 = min(o_warp + 16 * b + r, n_om - 1), i1 = min(o_warp + 16 * b + r + 8, n_om - 1);
       omh[b] = make_float2(__ldg(J.om_tab + i0), __ldg(J.om_tab + i1));
-      nomh[b] = make_float2(__ldg(J.om_tab + n_om + i0), __ldg(J.om_tab + n_om + i1));
-      wh[b] = make_float2(__ldg(J.om_tab + 2 * n_om + i0), __ldg(J.om_tab + 2 * n_om + i1));
-      wl[b] = make_float2(__ldg(J.om_tab + 3 * n_om + i0), __ldg(J.om_tab + 3 * n_om + i1));
+      wh[b] = make_float2(__ldg(J.om_tab + n_om + i0), __ldg(J.om_tab + n_om + i1));
+      wl[b] = make_float2(__ldg(J.om_tab + 2 * n_om + i0), __ldg(J.om_tab + 2 * n_om + i1));
     }
   };
   load_omega(o_warp0);
@@ -488,7 +491,7 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
 #pragma unroll
     for (int e = 0; e < 4; ++e) dre[b][e] = dim[b][e] = 0.0f;
 #pragma unroll
-  for (int v = 0; v < 4 * PASSES; ++v) l2[v * THREADS + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int v = 0; v < GQ * PASSES; ++v) l2[v * THREADS + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   const long long k_begin = (long long)chunk * K.ck;
   const long long k_end = min(k_begin + (long long)K.ck, K.n);
@@ -545,8 +548,8 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
             const float2 thB = make_float2(tB.x, tB.x), tlB = make_float2(tB.y, tB.y);
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-              const float2 pA = phase2(omh[b], nomh[b], wh[b], wl[b], thA, tlA);
-              const float2 pB = phase2(omh[b], nomh[b], wh[b], wl[b], thB, tlB);
+              const float2 pA = phase2(omh[b], wh[b], wl[b], thA, tlA);
+              const float2 pB = phase2(omh[b], wh[b], wl[b], thB, tlB);
               tc_block(pA, pB, b0, b1, dre[b], dim[b]);
             }
           }
@@ -576,7 +579,7 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
           }
         }
       }
-      float4* l2p = l2 + ps * 4 * THREADS + threadIdx.x;
+      float4* l2p = l2 + ps * GQ * THREADS + threadIdx.x;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         float4 x = l2p[b * THREADS], y = l2p[(NB + b) * THREADS];
@@ -603,7 +606,7 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
   for (int b = 0; b < NB; ++b)
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const float* l2p = reinterpret_cast<const float*>(l2 + ps * 4 * THREADS + threadIdx.x);
+      const float* l2p = reinterpret_cast<const float*>(l2 + ps * GQ * THREADS + threadIdx.x);
       const float lre = l2p[4 * b * THREADS + e];
       const float lim = l2p[4 * (NB + b) * THREADS + e];
       const float re = lre + __shfl_xor_sync(0xffffffffu, lre, 2);
@@ -616,7 +619,7 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
         part[(size_t)(2 * j + 1) * nb + bin] = im;
       }
     }
-  if (last_arrival<THREADS>(J, K, tile, s_flag)) tile_epilogue<THREADS>(J, K, tile);
+  if (last_arrival<THREADS>(J, K, tile, s_flag)) tile_epilogue<THREADS, true>(J, K, tile);
   return true;
 }
 
@@ -656,7 +659,8 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     const int chunk = (int)(local % K.n_chunks);
     const int tile = (int)(local / K.n_chunks);
     bool ok;
-    if constexpr (TC) ok = process_item_tc<THREADS, PASSES>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
+    if constexpr (TC)
+      ok = process_item_tc<THREADS, PASSES, 2 * W>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
     else ok = process_item_fma<THREADS, W, 2, LIT>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
     if (!ok) break;
   }
@@ -668,7 +672,7 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
 
 template <int T, int W, int MINB, bool TC, bool LIT, int P = 1>
 cudaError_t launch_acc(const LaunchArgs& a, int grid, cudaStream_t s) {
-  const size_t smem = Smem<T, TC, LIT, P>::bytes;
+  const size_t smem = Smem<T, TC, LIT, TC ? P * W : P>::bytes;
   // The shared-memory opt-in is per kernel and device, and idempotent.
   static std::atomic<bool> attr_set[kMaxDevices];
   const int dev = current_device();
@@ -686,7 +690,7 @@ cudaError_t launch_acc(const LaunchArgs& a, int grid, cudaStream_t s) {
 template <int T, int W, int MINB, bool TC, bool LIT, int P = 1>
 int blocks_per_sm() {
   int nb = 0;
-  const size_t smem = Smem<T, TC, LIT, P>::bytes;
+  const size_t smem = Smem<T, TC, LIT, TC ? P * W : P>::bytes;
   cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accumulate_kernel<T, W, MINB, TC, LIT, P>, T,
@@ -701,14 +705,16 @@ int blocks_per_sm() {
 // Variants (rad_impl.h: variant_info): 0 FP32 256x2, 1 FP32 256x4, 2 FP32 128x2,
 // 3 tensor-core 256 (3 CTAs/SM), 4 tensor-core 256 (4 CTAs/SM), 5 FP32 256x2 (4 CTAs/SM),
 // 6 FP32 256x2 with the literal sum (2 CTAs/SM), 7 tensor-core 256 sweeping each staged
-// particle tile in two frequency passes.
+// particle tile in two frequency passes, 8 tensor-core 256 with four 16-frequency blocks
+// per warp (512 frequencies per tile, 2 CTAs/SM).
 size_t accumulate_smem_bytes(int variant) {
   switch (variant) {
     case 2: return Smem<128, false>::bytes;
     case 3:
     case 4: return Smem<256, true>::bytes;
     case 6: return Smem<256, false, true>::bytes;
-    case 7: return Smem<256, true, false, 2>::bytes;
+    case 7:
+    case 8: return Smem<256, true, false, 2>::bytes;
     default: return Smem<256, false>::bytes;
   }
 }
@@ -731,6 +737,7 @@ int accumulate_blocks_per_sm(int variant) {
     case 5: nb = blocks_per_sm<256, 2, 4, false, false>(); break;
     case 6: nb = blocks_per_sm<256, 2, 2, false, true>(); break;
     case 7: nb = blocks_per_sm<256, 1, 3, true, false, 2>(); break;
+    case 8: nb = blocks_per_sm<256, 2, 2, true, false>(); break;
     default: nb = blocks_per_sm<256, 2, 3, false, false>(); break;
   }
   if (cache) cached[dev][variant].store(nb, std::memory_order_relaxed);
@@ -746,6 +753,7 @@ cudaError_t launch_accumulate(int variant, const LaunchArgs& a, int grid, cudaSt
     case 5: return launch_acc<256, 2, 4, false, false>(a, grid, s);
     case 6: return launch_acc<256, 2, 2, false, true>(a, grid, s);
     case 7: return launch_acc<256, 1, 3, true, false, 2>(a, grid, s);
+    case 8: return launch_acc<256, 2, 2, true, false>(a, grid, s);
     default: return launch_acc<256, 2, 3, false, false>(a, grid, s);
   }
 }

@@ -383,7 +383,7 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
   c->tile.omega_tile = default_omega_tile(kDefaultVariant, n_omega);
   c->tile.chunk = 0;
 
-  // Frequency table: omega/2pi split hi/lo; (hi, -hi, 2pi hi, 2pi lo) floats.
+  // Frequency table: omega/2pi split hi/lo; (hi, 2pi hi, 2pi lo) floats.
   std::vector<float> om_tab((size_t)kOmTab * n_omega);
   std::vector<double> om_turns(n_omega);
   double om_hi_max = 0.0;
@@ -393,9 +393,8 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
     const float lo = (float)(turns - (double)hi);
     om_turns[i] = turns;
     om_tab[i] = hi;
-    om_tab[n_omega + i] = -hi;
-    om_tab[2 * n_omega + i] = (float)(kTwoPi * (double)hi);
-    om_tab[3 * n_omega + i] = (float)(kTwoPi * (double)lo);
+    om_tab[n_omega + i] = (float)(kTwoPi * (double)hi);
+    om_tab[2 * n_omega + i] = (float)(kTwoPi * (double)lo);
     om_hi_max = std::max(om_hi_max, (double)fabsf(hi));
   }
   // Direction table: n (hi, lo) and a transverse orthonormal basis (e1, e2).

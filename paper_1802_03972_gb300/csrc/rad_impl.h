@@ -25,7 +25,7 @@ namespace radimpl {
 constexpr int kRecFields = 20;
 constexpr int kComps = 8;
 constexpr int kDirTab = 12;
-constexpr int kOmTab = 4;
+constexpr int kOmTab = 3;
 // Work items hold a multiple of 256 macro-particles: a whole number of
 // shared-memory tiles (threads / directions-per-tile particles) for every
 // kernel variant and tile shape.
@@ -99,10 +99,11 @@ struct Variant {
 // tiling rules: bins per tile = threads x w x passes, frequency tiles multiples
 // of 32 w passes);
 // 6: FP32-FMA with the paper's literal sum as well (literal contexts only);
-// 7: tensor-core accumulation in two frequency passes per staged particle tile.
-constexpr int kNumVariants = 8;
+// 7: tensor-core accumulation in two frequency passes per staged particle tile;
+// 8: tensor-core accumulation, a warp covers 64 frequencies (w = 2), 2 CTAs/SM.
+constexpr int kNumVariants = 9;
 constexpr int kLiteralVariant = 6;
-constexpr int kDefaultVariant = 7;  // a new context's tile, and a mixed batch's
+constexpr int kDefaultVariant = 8;  // a new context's tile, and a mixed batch's
 inline Variant variant_info(int v) {
   switch (v) {
     case 1: return {256, 4, 1};
@@ -110,6 +111,7 @@ inline Variant variant_info(int v) {
     case 3:
     case 4: return {256, 1, 1};
     case 7: return {256, 1, 2};
+    case 8: return {256, 2, 1};
     default: return {256, 2, 1};
   }
 }

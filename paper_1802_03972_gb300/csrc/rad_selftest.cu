@@ -50,7 +50,7 @@ __global__ void selftest_record_kernel(const float* __restrict__ rec, long long 
   o[7] = 0.f;
 }
 
-// om_tab rows: omega/2pi hi, -hi, 2pi hi, 2pi lo (floats); om_turns: omega/2pi (double).
+// om_tab rows: omega/2pi hi, 2pi hi, 2pi lo (floats); om_turns: omega/2pi (double).
 __global__ void selftest_phase_kernel(const float* __restrict__ om_tab,
                                       const double* __restrict__ om_turns, int n_omega,
                                       const float* __restrict__ th, const float* __restrict__ tl,
@@ -58,10 +58,10 @@ __global__ void selftest_phase_kernel(const float* __restrict__ om_tab,
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n_omega * n_tau) return;
   const int i = (int)(idx / n_tau), j = (int)(idx - (long long)i * n_tau);
-  const float h = om_tab[i], nh = om_tab[n_omega + i];
-  const float wh = om_tab[2 * n_omega + i], wl = om_tab[3 * n_omega + i];
-  const float2 p = phase2(make_float2(h, h), make_float2(nh, nh), make_float2(wh, wh),
-                          make_float2(wl, wl), make_float2(th[j], th[j]), make_float2(tl[j], tl[j]));
+  const float h = om_tab[i];
+  const float wh = om_tab[n_omega + i], wl = om_tab[2 * n_omega + i];
+  const float2 p = phase2(make_float2(h, h), make_float2(wh, wh), make_float2(wl, wl),
+                          make_float2(th[j], th[j]), make_float2(tl[j], tl[j]));
   fast[idx] = p.x;
   wide[idx] = phase_wide(om_turns[i], th[j], tl[j]);
 }

@@ -81,15 +81,13 @@ __device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
 
 // Phase of a frequency pair (packed) for one particle: returns radians in
 // (-pi, pi] + a tiny cross-term excess.
-__device__ __forceinline__ float2 phase2(float2 omh, float2 nomh, float2 wh, float2 wl, float2 th,
-                                         float2 tl) {
+__device__ __forceinline__ float2 phase2(float2 omh, float2 wh, float2 wl, float2 th, float2 tl) {
   const float2 kMag = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23
-  const float2 kNegMag = make_float2(-12582912.0f, -12582912.0f);
   const float2 k2Pi = make_float2(6.28318530717958647692f, 6.28318530717958647692f);
-  const float2 t0 = __ffma2_rn(nomh, th, kMag);  // 1.5*2^23 - rint(x)
-  const float2 q = __fadd2_rn(t0, kNegMag);       // -rint(x), exact
-  const float2 f0 = __ffma2_rn(omh, th, q);       // x - rint(x), one rounding
-  const float2 c1 = __fmul2_rn(wl, th);           // cross terms, radians
+  const float2 t0 = __ffma2_rn(omh, th, kMag);                     // 1.5*2^23 + rint(x)
+  const float2 q = __fadd2_rn(kMag, make_float2(-t0.x, -t0.y));   // -rint(x), exact
+  const float2 f0 = __ffma2_rn(omh, th, q);                        // x - rint(x), one rounding
+  const float2 c1 = __fmul2_rn(wl, th);                            // cross terms, radians
   const float2 c2 = __ffma2_rn(wh, tl, c1);
   return __ffma2_rn(f0, k2Pi, c2);
 }

@@ -23,8 +23,8 @@ constexpr size_t kOffJob = 0;                                   // JobStatic
 constexpr size_t kOffRef = 1024;                                // double[4]
 constexpr size_t kOffStatus = kOffRef + 32;                     // int
 constexpr size_t kOffCounter = kOffRef + 40;                    // unsigned long long
-constexpr size_t kOffOmTab = 1280;                              // float[4][MAX_OMEGA]
-constexpr size_t kOffOmTurns = kOffOmTab + 4 * 4 * RAD_STATIC_MAX_OMEGA;    // double[MAX_OMEGA]
+constexpr size_t kOffOmTab = 1280;                              // float[kOmTab][MAX_OMEGA]
+constexpr size_t kOffOmTurns = kOffOmTab + 4 * kOmTab * RAD_STATIC_MAX_OMEGA;  // double[MAX_OMEGA]
 constexpr size_t kOffDirTab = kOffOmTurns + 8 * RAD_STATIC_MAX_OMEGA;       // float[12][MAX_DIRS]
 constexpr size_t kOffDirs = kOffDirTab + 4 * 12 * RAD_STATIC_MAX_DIRS;      // double[MAX_DIRS][3]
 constexpr int kMaxTiles = 8192;
@@ -84,9 +84,8 @@ __global__ void __launch_bounds__(1024) static_setup_kernel(const double* __rest
     const float lo = __double2float_rn(turns - (double)hi);
     om_turns[i] = turns;
     om_tab[i] = hi;
-    om_tab[no + i] = -hi;
-    om_tab[2 * no + i] = __double2float_rn(kTwoPi * (double)hi);
-    om_tab[3 * no + i] = __double2float_rn(kTwoPi * (double)lo);
+    om_tab[no + i] = __double2float_rn(kTwoPi * (double)hi);
+    om_tab[2 * no + i] = __double2float_rn(kTwoPi * (double)lo);
     mx = fmaxf(mx, fabsf(hi));
   }
   for (int d = threadIdx.x; d < ndir; d += blockDim.x) {

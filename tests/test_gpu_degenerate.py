@@ -1,5 +1,5 @@
 """Degenerate cases of the radiation sum on the GPU, checked against what the
-mathematics fixes at any size (Eq. 1, Eq. 2, Eq. 12), on the FP32 and both
+mathematics fixes at any size (Eq. 1, Eq. 2, Eq. 12), on the FP32 and three
 tensor-core kernel variants:
 
 * beta_dot = 0: the amplitude n x ((n - beta) x beta_dot) / (1 - beta.n)^2
@@ -25,7 +25,7 @@ from paper_1802_03972_gb300 import build as _build  # noqa: E402
 _build.build()
 from paper_1802_03972_gb300 import rad  # noqa: E402
 
-VARIANTS = [0, 3, 7]
+VARIANTS = [0, 3, 7, 8]
 
 
 def run(omega, dirs, steps, variant, ff=(rad.FF_POINT, 0.0), scale_w=1.0, repeat=1):
