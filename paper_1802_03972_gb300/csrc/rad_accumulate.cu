@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     bool ok;
     if constexpr (TC)
       ok = process_item_tc<THREADS, PASSES, 2 * W>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
-    else ok = process_item_fma<THREADS, W, 2, LIT>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
+    else ok = process_item_fma<THREADS, W, 8, LIT>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
     if (!ok) break;
   }
   if (a.prof_clk && threadIdx.x == 0) {
