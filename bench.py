@@ -45,7 +45,9 @@ VARIANT_NAMES = {0: "FP32 FMA, 256 threads x 2 omega, 3 CTAs/SM",
                     "two frequency passes per staged particle tile",
                  8: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads x 2 omega "
                     "(64 per warp), 2 CTAs/SM"}
-KERNEL_SRC = os.path.join(ROOT, "paper_1802_03972_gb300", "csrc", "rad_accumulate.cu")
+# The accumulate kernel's sources: the kernel file and the headers its device code comes from.
+KERNEL_SRC = [os.path.join(ROOT, "paper_1802_03972_gb300", "csrc", f)
+              for f in ("rad_accumulate.cu", "rad_stage.cuh", "rad_device.cuh", "rad_impl.h")]
 
 
 def parse():
@@ -135,7 +137,10 @@ class Clocks:
 
 
 def kernel_hash() -> str:
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in KERNEL_SRC:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def traffic_per_launch(updates_per_step: int, tile):

@@ -484,7 +484,7 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
   load_omega(o_warp0);
   float dre[NB][4], dim[NB][4];
   // second-level sums of pass p: group q (q = b for the real parts of block b,
-  // NB + b for the imaginary parts) of this thread at l2[(p * 4 + q) * THREADS + threadIdx.x]
+  // NB + b for the imaginary parts) of this thread at l2[(p * GQ + q) * THREADS + threadIdx.x]
   float4* l2 = reinterpret_cast<float4*>(smem + S::raw_bytes + 2 * S::rec_bytes);
 #pragma unroll
   for (int b = 0; b < NB; ++b)

@@ -76,7 +76,8 @@ __device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
 // for packed arithmetic); tensor-core variants: float2 dtau + 8 floats of
 // amplitude hi/lo parts.
 // Tensor-core variants also keep their per-chunk (second-level) sums in
-// shared memory: 16 floats per thread, one slot per thread and value.
+// shared memory: 8 floats per thread and 16-frequency block of a warp (16 or
+// 32 per thread), one slot per thread and value.
 // The literal variant adds a fourth float4 per record: (w - 1) duplicated.
 
 // Phase of a frequency pair (packed) for one particle: returns radians in
