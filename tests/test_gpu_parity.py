@@ -153,6 +153,27 @@ def test_edge_cases_small_sizes():
         check(ctx, ref)
 
 
+@pytest.mark.parametrize("variant", [3, 8])
+def test_changing_particle_counts_between_calls(variant):
+    """One context fed calls of 3000, 700, 3000, 257 and 1 particles with a fixed
+    chunk of 512: the number of chunks, and so of partial-sum slots each tile's
+    last arrival adds up (and then drops from L2), changes from call to call;
+    every call must use only the slots it wrote."""
+    wl = small_lwfa(n=3000, n_omega=200, n_side=3, seed=24)
+    bo, bd = oracle.grid_bins(wl.omega, wl.dirs)
+    acc = oracle.Accumulator(bo, bd, wl.ff_kind, wl.ff_width)
+    ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
+    ctx.set_tile(variant, 0, 512)
+    for s, n in enumerate((3000, 700, 3000, 257, 1)):
+        st = wl.step(s)
+        cut = [a.reshape(3, -1)[:, :n] for a in (st.r, st.beta, st.beta_dot)]
+        acc.accumulate(*cut, st.w[:n], st.t, st.dt)
+        ctx.accumulate(*(to_dev(np.ascontiguousarray(a).ravel()) for a in cut), to_dev(st.w[:n]),
+                       st.t, st.dt)
+    ref = spectra_grid(acc, wl)
+    check(ctx, ref)
+
+
 def test_invalid_particles_reported_and_skipped():
     wl = small_lwfa(n=300, n_omega=64, n_side=2)
     good = oracle_run(wl, range(3))
