@@ -54,3 +54,30 @@ def test_binding_fails_loudly_without_library(tmp_path):
             rad.load(str(tmp_path / "missing.so"))
         finally:
             rad._lib = rad._lib_saved
+
+
+def build_c_client(out_dir):
+    """Compiles tests/c_abi_client.c as C11 against include/rad.h and links it
+    to the library; returns the executable's path."""
+    import shutil
+    import subprocess
+    from paper_1802_03972_gb300 import build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib = build.build()
+    libdir = os.path.dirname(lib)
+    exe = os.path.join(str(out_dir), "c_abi_client")
+    cmd = [cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "c_abi_client.c"), "-o", exe, "-L", libdir, "-lrad",
+           "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+def test_header_compiles_as_c_and_client_links(tmp_path):
+    import subprocess
+    exe = build_c_client(tmp_path)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 2 and "usage" in r.stderr
