@@ -137,9 +137,15 @@ class Clocks:
 
 
 def kernel_hash() -> str:
+    """Hash of the kernel's code: its sources with comments and blank space
+    removed, so that editing a comment does not orphan a capture."""
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SRC:
-        h.update(open(f, "rb").read())
+        src = open(f, encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -24,9 +24,9 @@
 // e^{i phi} are then formed in one of two ways:
 //  * FP32 variants: 8 packed FMAs (f32x2) per update into register accumulators,
 //    two frequencies per packed lane pair;
-//  * tensor-core variants: per warp, a 16-frequency x 8-particle block of
-//    e^{i phi} is the A operand of mma.sync m16n8k8 TF32 and the 4 weighted
-//    amplitudes of the 8 particles are B.  Both are split into TF32 hi and lo
+//  * tensor-core variants: per warp, each 16-frequency x 8-particle block of
+//    e^{i phi} (two or four blocks per warp) is the A operand of mma.sync
+//    m16n8k8 TF32 and the 4 weighted amplitudes of the 8 particles are B.  Both are split into TF32 hi and lo
 //    parts (hi = the top 19 bits, lo = the exact rest), B's hi and lo side by
 //    side in the 8 N-columns, so two MMAs per cos/sin give all of
 //    hi.hi + hi.lo + lo.hi + lo.lo with FP32 accumulation.  This takes the
@@ -37,7 +37,9 @@
 // counter, no float atomics) adds the partials in chunk order, multiplies by
 // e^{i omega tau_ref(n)} (reduced in FP64) and adds the result into the
 // resident state with compensated (Kahan) FP32 sums.  Results are
-// deterministic for a given tile configuration.
+// deterministic for a given tile configuration.  Work items are handed out
+// tile-major, so a tile's partials are still in L2 when they are added up;
+// the tensor-core variants then drop those lines from L2 unwritten.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
