@@ -452,7 +452,7 @@ class Server:
         self._h, self._lib = h, lib
 
     def set_policy(self, policy: int, round_updates: int = 0) -> None:
-        """rad_server_set_policy: SERVE_ALL, SERVE_OLDEST or SERVE_LEAST_SERVED."""
+        """rad_server_set_policy: SERVE_ALL, SERVE_OLDEST, SERVE_LEAST_SERVED or SERVE_LEAST_SERVED_AGED."""
         _check(self._lib.rad_server_set_policy(self._h, int(policy), int(round_updates)),
                "rad_server_set_policy")
 
