@@ -40,6 +40,10 @@
  *  - Objects are not thread-safe: one thread at a time per object.  Distinct
  *    objects are independent.  Work runs on the CUDA stream given at creation
  *    (NULL = the legacy default stream), in stream order.
+ *  - An object belongs to the CUDA device that is current when it is created:
+ *    calls on a context (and rad_job_feed on a server) made with another
+ *    device current return RAD_EINVAL, and a batch takes contexts of one
+ *    device.  A server's worker thread runs on the server's device.
  */
 #ifndef RAD_H
 #define RAD_H

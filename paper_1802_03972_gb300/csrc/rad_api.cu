@@ -92,6 +92,14 @@ int current_device() {
   return dev;
 }
 
+rad_status check_device(rad_ctx* c) {
+  const int d = current_device();
+  if (d == c->device) return RAD_OK;
+  rad_log(1, "a context of device %d was used with device %d current", c->device, d);
+  c->last_err = RAD_EINVAL;
+  return RAD_EINVAL;
+}
+
 rad_status fail(rad_ctx* c, rad_status s) {
   if (c) {
     c->last_err = s;
@@ -372,6 +380,7 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
     mix(omega, sizeof(double) * (size_t)n_omega);
     mix(nd.data(), sizeof(double) * nd.size());
     c->grid_hash = h;
+    c->device = current_device();
   }
   c->n_omega = n_omega;
   c->n_dir = n_dir;
@@ -525,6 +534,7 @@ rad_status rad_accumulate(rad_ctx* c, int64_t n, const double* r, const double* 
   radimpl::TraceRange trace("rad_accumulate");
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   if (n < 0 || !isfinite(t) || !isfinite(dt) || !(dt > 0.0)) return fail(c, RAD_EINVAL);
   if (n == 0) return RAD_OK;
   if (!r || !beta || !beta_dot || !w) return fail(c, RAD_EINVAL);
@@ -558,6 +568,7 @@ static rad_status check_status_word(rad_ctx* c) {
 rad_status rad_sync(rad_ctx* c) {
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   rad_status s = cuda_check(c, cudaStreamSynchronize(c->stream));
   if (s != RAD_OK) return s;
   return check_status_word(c);
@@ -567,6 +578,7 @@ rad_status rad_spectrum_ff(rad_ctx* c, rad_ff ff, double* coh, double* inc, doub
   radimpl::TraceRange trace("rad_spectrum");
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   // RAD_FF_LITERAL only matters at creation; the readout ignores it.
   if (ff.kind < RAD_FF_POINT || ff.kind > RAD_FF_GAUSS || !(ff.width >= 0.0) ||
       !isfinite(ff.width) || (ff.flags & ~(RAD_FF_3D | RAD_FF_LITERAL)) != 0)
@@ -606,6 +618,7 @@ rad_status rad_spectrum_species(rad_ctx* const* ctxs, const rad_ff* ffs, int32_t
     const rad_ff& ff = ffs[i];
     if (!c) return RAD_EINVAL;
     if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
     if (c->n_omega != c0->n_omega || c->n_dir != c0->n_dir || c->grid_hash != c0->grid_hash ||
         c->prec != c0->prec)
       return fail(c0, RAD_EINVAL);
@@ -656,6 +669,7 @@ rad_status rad_spectrum(rad_ctx* c, double* coh, double* inc, double* tot) {
 rad_status rad_reset(rad_ctx* c) {
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   cudaError_t e = (c->prec == RAD_PREC_MIXED)
                       ? cudaMemsetAsync(c->d_state, 0, sizeof(float) * 2 * kComps * c->n_bins, c->stream)
                       : cudaMemsetAsync(c->d_state64, 0, sizeof(double) * 12 * c->n_bins, c->stream);
@@ -674,6 +688,7 @@ rad_status rad_spectrum_literal(rad_ctx* c, double* out) {
   radimpl::TraceRange trace("rad_spectrum_literal");
   if (!c || !out) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   if (!c->d_state_p) return fail(c, RAD_ESTATE);
   const bool host = !is_device_ptr(out);
   double* dst = host ? c->d_spec : out;
@@ -692,6 +707,7 @@ rad_status rad_last_error(const rad_ctx* c) { return c ? c->last_err : RAD_EINVA
 rad_status rad_profile_enable(rad_ctx* c, int32_t on) {
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   if (on && !c->d_prof_clk) {
     rad_status s = cuda_check(c, cudaMalloc(&c->d_prof_clk, 2 * sizeof(unsigned long long)));
     if (s == RAD_OK)
@@ -705,6 +721,7 @@ rad_status rad_profile_enable(rad_ctx* c, int32_t on) {
 rad_status rad_profile_clock(rad_ctx* c, double* sm_mhz) {
   if (!c || !sm_mhz) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   *sm_mhz = 0.0;
   if (!c->d_prof_clk) return RAD_OK;
   unsigned long long h[2] = {0, 0};
@@ -721,6 +738,7 @@ rad_status rad_profile_read(rad_ctx* c, double* prepass_ms, double* accumulate_m
                             int64_t* calls) {
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   rad_status s = cuda_check(c, cudaStreamSynchronize(c->stream));
   if (s != RAD_OK) return s;
   double pp = 0.0, ac = 0.0;
@@ -756,6 +774,7 @@ size_t rad_state_size(const rad_ctx* c) {
 rad_status rad_state_export(rad_ctx* c, void* buf, size_t n) {
   if (!c || !buf) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   if (n < rad_state_size(c)) return fail(c, RAD_EINVAL);
   BlobHeader h;
   memset(&h, 0, sizeof(h));
@@ -796,6 +815,7 @@ static rad_status check_blob(rad_ctx* c, const void* buf, size_t n) {
 rad_status rad_state_import(rad_ctx* c, const void* buf, size_t n) {
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   if (check_blob(c, buf, n) != RAD_OK) return fail(c, RAD_EINVAL);
   void* dst = c->prec == RAD_PREC_MIXED ? (void*)c->d_state : (void*)c->d_state64;
   rad_status s = cuda_check(c, cudaMemcpyAsync(dst, (const char*)buf + sizeof(BlobHeader),
@@ -815,6 +835,7 @@ rad_status rad_state_import(rad_ctx* c, const void* buf, size_t n) {
 rad_status rad_state_merge(rad_ctx* c, const void* buf, size_t n) {
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   if (check_blob(c, buf, n) != RAD_OK) return fail(c, RAD_EINVAL);
   void* tmp = nullptr;
   rad_status s = cuda_check(c, cudaMalloc(&tmp, payload_bytes(c)));
@@ -846,6 +867,7 @@ rad_status rad_get_tile(const rad_ctx* c, rad_tile* t) {
 rad_status rad_set_tile(rad_ctx* c, const rad_tile* t) {
   if (!c || !t) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   if (c->prec != RAD_PREC_MIXED) return fail(c, RAD_EINVAL);
   if (t->variant < 0 || t->variant >= kNumVariants) return fail(c, RAD_EINVAL);
   // The literal sum has its own kernel variant, used only by literal contexts.

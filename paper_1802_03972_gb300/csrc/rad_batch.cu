@@ -255,6 +255,7 @@ rad_status rad_batch_create(rad_ctx* const* ctxs, int32_t n_jobs, void* stream, 
   for (int i = 0; i < n_jobs; ++i) {
     if (!ctxs[i] || ctxs[i]->prec != RAD_PREC_MIXED || ctxs[i]->failed || ctxs[i]->h_js.literal)
       return RAD_EINVAL;
+    if (check_device(ctxs[i]) != RAD_OK) return RAD_EINVAL;  // one device for the whole batch
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return RAD_EINVAL;
   }
@@ -278,6 +279,7 @@ rad_status rad_batch_accumulate(rad_batch* b, const rad_step* steps) {
     if (st.n < 0 || !isfinite(st.t) || !isfinite(st.dt) || !(st.dt > 0.0)) return RAD_EINVAL;
     if (st.n > 0 && (!st.r || !st.beta || !st.beta_dot || !st.w)) return RAD_EINVAL;
     if (b->jobs[i]->failed) return RAD_ESTATE;
+    if (check_device(b->jobs[i]) != RAD_OK) return RAD_EINVAL;
   }
   TraceRange trace("rad_batch_accumulate");
   rad_status s = b->core.run(b->jobs.data(), steps, (int)b->jobs.size(), true);

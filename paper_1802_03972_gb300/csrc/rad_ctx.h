@@ -50,6 +50,7 @@ struct rad_ctx {
   unsigned long long* d_prof_clk = nullptr;  // [2] cycles, ns of the accumulate CTAs
   long long generation = 0;      // bumped whenever d_js changes
   uint64_t grid_hash = 0;        // FNV-1a of the frequencies and unit directions
+  int device = -1;               // the CUDA device current at rad_create
   rad_status last_err = RAD_OK;
   bool failed = false;
 };
@@ -66,6 +67,9 @@ struct TraceRange {
 };
 
 rad_status fail(rad_ctx* c, rad_status s);
+// RAD_OK when the context's device is the calling thread's current device;
+// otherwise RAD_EINVAL (its memory, stream and kernels belong to that device).
+rad_status check_device(rad_ctx* c);
 rad_status cuda_check(rad_ctx* c, cudaError_t e);
 int default_omega_tile(int variant, int n_omega);
 bool valid_omega_tile(int variant, int wt);

@@ -48,6 +48,7 @@ rad_status rad_push_step(rad_ctx* c, int64_t n, const double* r, const double* b
                          const double* w, double t, double dt) {
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   if (n < 1 || !r || !beta || !w || !isfinite(t) || !isfinite(dt) || !(dt > 0.0))
     return fail(c, RAD_EINVAL);
   if (c->push_held > 0 && n != c->n_push) return fail(c, RAD_EINVAL);
@@ -105,6 +106,7 @@ rad_status rad_push_step(rad_ctx* c, int64_t n, const double* r, const double* b
 rad_status rad_push_flush(rad_ctx* c) {
   if (!c) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   rad_status s = RAD_OK;
   if (c->push_held == 2) {
     // last step: backward difference

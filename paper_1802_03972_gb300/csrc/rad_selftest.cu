@@ -105,6 +105,7 @@ rad_status rad_selftest_stage1(rad_ctx* c, int64_t n, const double* r, const dou
                                int32_t dir, float* out, float* basis) {
   if (!c || !out || !basis || !r || !beta || !beta_dot || !w) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   if (c->prec != RAD_PREC_MIXED || n < 1 || n > (1 << 20) || dir < 0 || dir >= c->n_dir)
     return RAD_EINVAL;
   rad_status s = ensure_capacity(c, n, 1);
@@ -149,6 +150,7 @@ rad_status rad_selftest_phase(rad_ctx* c, int32_t n_tau, const float* th, const 
                               float* fast, float* wide) {
   if (!c || !th || !tl || !fast || !wide) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   if (c->prec != RAD_PREC_MIXED || n_tau < 1 || n_tau > (1 << 20)) return RAD_EINVAL;
   const size_t m = (size_t)c->n_omega * (size_t)n_tau;
   float *d_th = nullptr, *d_tl = nullptr, *d_f = nullptr, *d_w = nullptr;

@@ -89,6 +89,7 @@ size_t estimate_footprint(const rad_job_desc& d) {
 }  // namespace
 
 struct rad_server {
+  int device = -1;  // the CUDA device current at rad_server_create; the worker runs on it
   size_t budget = 0;
   int max_slots = 1;
   cudaStream_t compute = nullptr;
@@ -304,6 +305,7 @@ rad_status rad_server_create(size_t hbm_budget, int32_t max_slots, void* stream,
   if (hbm_budget == 0 || max_slots < 1) return RAD_EINVAL;
   rad_server* s = new (std::nothrow) rad_server();
   if (!s) return RAD_ENOMEM;
+  s->device = current_device();
   s->budget = hbm_budget;
   s->max_slots = max_slots;
   s->compute = (cudaStream_t)stream;
@@ -327,7 +329,10 @@ rad_status rad_server_create(size_t hbm_budget, int32_t max_slots, void* stream,
     delete s;
     return st;
   }
-  s->worker = std::thread([s] { s->loop(); });
+  s->worker = std::thread([s] {
+    if (s->device >= 0) cudaSetDevice(s->device);  // a new thread starts on device 0
+    s->loop();
+  });
   *out = s;
   return RAD_OK;
 }
@@ -371,6 +376,7 @@ rad_status rad_job_submit(rad_server* s, const rad_job_desc* d, rad_job_id* id) 
 
 rad_status rad_job_feed(rad_server* s, rad_job_id id, const rad_step* step) {
   if (!s || !step) return RAD_EINVAL;
+  if (current_device() != s->device) return RAD_EINVAL;  // the server's copies run on its device
   if (step->n < 0 || !isfinite(step->t) || !isfinite(step->dt) || !(step->dt > 0.0))
     return RAD_EINVAL;
   if (step->n > 0 && (!step->r || !step->beta || !step->beta_dot || !step->w)) return RAD_EINVAL;

@@ -94,6 +94,7 @@ __global__ void fill_synthetic(long long n, double* r, double* beta, double* bdo
 extern "C" rad_status rad_tune(rad_ctx* c, int64_t n) {
   if (!c || n < 1) return RAD_EINVAL;
   if (c->failed) return RAD_ESTATE;
+  if (check_device(c) != RAD_OK) return RAD_EINVAL;
   if (c->prec != RAD_PREC_MIXED) return RAD_OK;  // the FP64 kernel has no tiles
   if (c->h_js.literal) return RAD_OK;             // the literal sum has one variant
   const Key key(c->n_omega, c->n_dir, bucket(n));
