@@ -230,8 +230,9 @@ typedef struct {
 rad_status rad_get_tile(const rad_ctx* ctx, rad_tile* tile);
 rad_status rad_set_tile(rad_ctx* ctx, const rad_tile* tile);
 
-/* rad_tune - time candidate tiles on synthetic particles of count n and keep
- * the fastest for this context's grid shape.  Results are cached per shape
+/* rad_tune - time candidate tiles on synthetic particles (n of them, or fewer
+ * when n x bins is large; the chunk size is then left automatic) and keep the
+ * fastest for this context's grid shape.  Results are cached per shape
  * bucket in memory and, when the environment variable RAD_TUNE_CACHE names a
  * file, on disk.  Leaves the accumulators unchanged. */
 rad_status rad_tune(rad_ctx* ctx, int64_t n);

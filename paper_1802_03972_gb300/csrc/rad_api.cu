@@ -150,7 +150,7 @@ int resident_ctas(int variant) {
 // multiple of the shared-memory tile.  Depends only on the job's shape, n and
 // the device, so a job is chunked the same way alone and in a batch.
 int auto_chunk_for(int variant, long long n, int n_tiles) {
-  const long long target = 16LL * resident_ctas(variant);
+  const long long target = (long long)kItemsPerCta * resident_ctas(variant);
   long long chunks = (target + n_tiles - 1) / n_tiles;
   const long long max_chunks = (n + kChunkAlign - 1) / kChunkAlign;
   chunks = std::max(1LL, std::min(chunks, max_chunks));

@@ -105,7 +105,7 @@ extern "C" rad_status rad_tune(rad_ctx* c, int64_t n) {
     if (it != g_cache.end()) return rad_set_tile(c, &it->second);
   }
   // Candidates: every variant, the default and half / double frequency tiles,
-  // automatic chunking and half / double of it.
+  // automatic chunking and half / double of it (see n_ckm below).
   std::vector<rad_tile> cands;
   for (int v = 0; v < kNumVariants; ++v) {
     if (v == kLiteralVariant) continue;
@@ -139,8 +139,12 @@ extern "C" rad_status rad_tune(rad_ctx* c, int64_t n) {
   }
   rad_tile best = orig;
   float best_ms = 1e30f;
+  // Half and double the automatic chunk are tried only when the trial runs the
+  // caller's particle count: the best chunk depends on it (the blocks' tail at
+  // the end of a launch), so one picked on a smaller trial does not carry over.
+  const int n_ckm = nt == n ? 3 : 1;
   for (size_t i = 0; st == RAD_OK && i < cands.size(); ++i) {
-    for (int ckm : {0, 1, 2}) {
+    for (int ckm = 0; ckm < n_ckm; ++ckm) {
       rad_tile t = cands[i];
       if (ckm) {
         JobStatic js = c->h_js;
