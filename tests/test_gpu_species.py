@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import TOL_FP64, TOL_TOTAL, gpu_run, oracle_run, row_error
+from gpu_util import TOL_FP64, TOL_TOTAL, gpu_run, oracle_run, row_error, to_dev
 from paper_1802_03972_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -106,3 +106,30 @@ def test_bad_species_arguments():
     # the refused calls leave the contexts usable
     coh, inc, tot = rad.spectrum_species([a, b], [ff, FFS[2]])
     assert np.all(np.isfinite(tot)) and np.all(tot > 0)
+
+
+def test_species_with_invalid_particles_reports_once_and_keeps_spectra():
+    """A species that saw invalid particles (NaN position, |beta| > 1): the
+    species readout writes the spectra of the valid particles and returns
+    RAD_EDATA once; the next readout is clean and identical."""
+    wls = species_workloads()
+    ref_accs = [oracle_run(wl, range(2)) for wl in wls[:2]]
+    shape = (wls[0].dirs.shape[0], wls[0].omega.shape[0])
+    ref = {k: v.reshape(shape) for k, v in oracle.species_spectra(ref_accs, FFS[:2]).items()}
+    good = gpu_run(wls[0], range(2))
+    bad = rad.Context(wls[1].omega, wls[1].dirs, wls[1].ff_kind, wls[1].ff_width)
+    for s in range(2):
+        st = wls[1].step(s)
+        r = np.concatenate([st.r.reshape(3, -1), np.array([[np.nan], [0.0], [0.0]])], 1)
+        b = np.concatenate([st.beta.reshape(3, -1), np.array([[0.0], [0.0], [1.5]])], 1)
+        bd = np.concatenate([st.beta_dot.reshape(3, -1), np.ones((3, 1)) * 1e13], 1)
+        w = np.concatenate([st.w, [10.0]])
+        bad.accumulate(to_dev(r), to_dev(b), to_dev(bd), to_dev(w), st.t, st.dt)
+    first = tuple(np.zeros(shape) for _ in range(3))
+    with pytest.raises(rad.RadError) as ei:
+        rad.spectrum_species([good, bad], FFS[:2], out=first)
+    assert ei.value.status == rad.RAD_EDATA
+    again = rad.spectrum_species([good, bad], FFS[:2])  # reported once: now clean
+    for k, a, b2 in zip(("coh", "inc", "tot"), first, again):
+        np.testing.assert_array_equal(a, b2)
+        assert row_error(a, ref[k]) <= TOL_TOTAL, k
