@@ -156,6 +156,7 @@ int auto_chunk_for(int variant, long long n, int n_tiles) {
   chunks = std::max(1LL, std::min(chunks, max_chunks));
   long long ck = (n + chunks - 1) / chunks;
   ck = (ck + kChunkAlign - 1) / kChunkAlign * kChunkAlign;
+  if (ck < kMinChunk && n > kMinChunk) ck = kMinChunk;
   if (ck > (1LL << 30)) ck = 1LL << 30;
   return (int)ck;
 }

@@ -32,8 +32,13 @@ constexpr int kOmTab = 3;
 constexpr int kChunkAlign = 256;
 // Automatic chunking aims at this many work items per resident block: enough
 // that the blocks finishing last wait on short items (measured on the LWFA
-// workload: 24 gave 7.13 ms per step, 16 gave 7.19).
+// workload: 24 gave 7.13 ms per step, 16 gave 7.19) ...
 constexpr int kItemsPerCta = 24;
+// ... but gives a work item at least this many particles, over which its fixed
+// costs (the first tile's exposed copy, zeroing and writing its partial sums)
+// spread: on the batched job mix of small jobs this measured 1 % faster.
+constexpr int kMinChunk = 2048;
+static_assert(kMinChunk % kChunkAlign == 0, "the minimum chunk is a whole number of tiles");
 
 // Device status bits (per job).
 enum : int { ST_BAD_PARTICLE = 1, ST_SLOW_PHASE = 2, ST_TIMEOUT = 4 };
