@@ -41,8 +41,8 @@
  *    objects are independent.  Work runs on the CUDA stream given at creation
  *    (NULL = the legacy default stream), in stream order.
  *  - Diagnostics: with the environment variable RAD_LOG=1 the library prints
- *    CUDA errors and refused calls to stderr; RAD_LOG=2 adds the tuner's
- *    choices and the server's admissions and completions.
+ *    CUDA errors, calls refused for the wrong device and the tuner's choices
+ *    to stderr; RAD_LOG=2 adds the server's admissions and completions.
  *  - An object belongs to the CUDA device that is current when it is created:
  *    calls on a context (and rad_job_feed on a server) made with another
  *    device current return RAD_EINVAL, and a batch takes contexts of one
