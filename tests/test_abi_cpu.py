@@ -151,3 +151,17 @@ def test_every_entry_point_refuses_null_handles_without_a_gpu():
     lib.rad_destroy(None)
     lib.rad_batch_destroy(None)
     lib.rad_server_destroy(None)
+
+
+def test_every_header_compiles_as_pedantic_c11(tmp_path):
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "all_headers.c"
+    src.write_text('#include "rad.h"\n#include "rad_probe.h"\n#include "rad_selftest.h"\n'
+                   "int main(void) { return 0; }\n")
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
