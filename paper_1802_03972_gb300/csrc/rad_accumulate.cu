@@ -144,6 +144,7 @@ template <int THREADS, bool DISCARD>
 __device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall& K, int tile) {
   const TileGeom g = tile_geom(J, tile, THREADS);
   const int nb = J.n_bins, n_om = J.n_omega;
+  if (!bounds_ok(K.n_chunks <= J.chunk_cap && tile < J.n_tiles, J.status)) return;
   for (int i = threadIdx.x; i < g.NT * g.WT; i += THREADS) {
     const int dl = i / g.WT;
     const int d = g.d0 + dl, o = g.o0 + (i - dl * g.WT);
@@ -204,6 +205,8 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // Loads one raw particle tile; thread 0 only.
 __device__ __forceinline__ void issue_tile(const JobStatic& J, long long k0, int KT, float* raw,
                                            uint64_t* bar) {
+  // (skipped in a debug build when out of range: the block's bounded wait then gives up)
+  if (!bounds_ok(k0 + KT <= J.n_cap, J.status)) return;
   tma_load_1d(raw, J.rec + (size_t)k0 * kRecFields, (uint32_t)KT * kRecFields * sizeof(float), bar);
 }
 
@@ -388,7 +391,7 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int o = om_first + 2 * p + e;
-        if (o < n_om) {
+        if (o < n_om && bounds_ok(chunk < J.chunk_cap, J.status)) {
           const int bin = my_d * n_om + o;
 #pragma unroll
           for (int c = 0; c < kComps; ++c)
@@ -617,7 +620,7 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
       const float im = lim + __shfl_xor_sync(0xffffffffu, lim, 2);
       const int o = o_warp0 + ps * PW + 16 * b + r + ((e >> 1) << 3);
       const int j = 2 * c + (e & 1);  // amplitude column
-      if (c < 2 && my_d_raw < J.n_dir && o < n_om) {
+      if (c < 2 && my_d_raw < J.n_dir && o < n_om && bounds_ok(chunk < J.chunk_cap, J.status)) {
         const int bin = my_d * n_om + o;
         part[(size_t)(2 * j) * nb + bin] = re;
         part[(size_t)(2 * j + 1) * nb + bin] = im;

@@ -552,6 +552,12 @@ static rad_status check_status_word(rad_ctx* c) {
   if (s != RAD_OK) return s;
   s = cuda_check(c, cudaStreamSynchronize(c->stream));
   if (s != RAD_OK) return s;
+  if (st & ST_BOUNDS) {
+    // A debug build's index check failed: a sizing error inside the library.
+    rad_log(1, "an index check of the debug build failed (status 0x%x)", st);
+    c->failed = true;
+    return fail(c, RAD_ECUDA);
+  }
   if (st & ST_TIMEOUT) {
     // A bounded wait in the kernel gave up: the accumulators are incomplete.
     c->failed = true;

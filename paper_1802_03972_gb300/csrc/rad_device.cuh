@@ -10,6 +10,19 @@
 namespace radimpl {
 namespace dev {
 
+// Debug builds (compiled with RAD_DEBUG_BOUNDS) check the global-memory
+// indices that depend on host-side sizing (record capacity, partial-sum slots,
+// bins): a failed check sets ST_BOUNDS in the job's status word and the access
+// is skipped.  Release builds compile the checks away.
+#ifdef RAD_DEBUG_BOUNDS
+__device__ __forceinline__ bool bounds_ok(bool cond, int* status) {
+  if (!cond) atomicOr(status, ST_BOUNDS);
+  return cond;
+}
+#else
+__device__ __forceinline__ bool bounds_ok(bool, int*) { return true; }
+#endif
+
 constexpr double kC = 299792458.0;
 constexpr double kInvC = 1.0 / 299792458.0;
 constexpr unsigned long long kWaitLimitNs = 1000000000ULL;  // 1 s bound on any wait

@@ -41,7 +41,8 @@ constexpr int kMinChunk = 2048;
 static_assert(kMinChunk % kChunkAlign == 0, "the minimum chunk is a whole number of tiles");
 
 // Device status bits (per job).
-enum : int { ST_BAD_PARTICLE = 1, ST_SLOW_PHASE = 2, ST_TIMEOUT = 4 };
+// ST_BOUNDS: an index check of a debug build (RAD_DEBUG_BOUNDS) failed.
+enum : int { ST_BAD_PARTICLE = 1, ST_SLOW_PHASE = 2, ST_TIMEOUT = 4, ST_BOUNDS = 8 };
 
 // Per-job data that does not change between calls.
 struct JobStatic {

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) prepass_kernel(LaunchArgs a) {
     v[15] = 0.75f;
   }
   v[19] = 0.0f;
+  if (!dev::bounds_ok(k < J.n_cap, J.status)) return;
   float4* dst = reinterpret_cast<float4*>(J.rec + (size_t)k * kRecFields);
 #pragma unroll
   for (int q = 0; q < kRecFields / 4; ++q)

@@ -14,7 +14,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librad.so")
+# The library the binding loads: librad.so, or another build of it (such as
+# librad_debug.so, with the kernels' index checks) named by RAD_LIBRARY.
+LIB_PATH = os.environ.get("RAD_LIBRARY") or os.path.join(_HERE, "librad.so")
 
 RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_EDATA, RAD_ETIMEOUT, RAD_EBUSY, RAD_ESTATE = range(8)
 FF_POINT, FF_CIC, FF_TSC, FF_QSC, FF_GAUSS = range(5)
