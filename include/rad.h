@@ -103,8 +103,11 @@ typedef struct {
 } rad_ff;
 
 typedef enum {
-  RAD_PREC_MIXED = 0, /* float-float retarded time and phase, FP32 sin/cos and
-                         sums, compensated accumulation over calls (default) */
+  RAD_PREC_MIXED = 0, /* float-float retarded time and phase, FP32 sin/cos; the
+                         sum over particles runs in FP32 (default kernel: on the
+                         tensor cores, mma.sync TF32 with both operands split
+                         into hi and lo parts, FP32 accumulation); compensated
+                         FP32 accumulation over calls (default) */
   RAD_PREC_FP64 = 1   /* plain kernel: everything in FP64, one thread per bin */
 } rad_prec;
 
@@ -379,9 +382,12 @@ rad_status rad_profile_clock(rad_ctx* ctx, double* sm_mhz);
  * device (cudaGetSymbolAddress), so make that first call before any stream
  * capture.  Every call shares the one array and clears what must start at zero.
  * Calls whose work overlaps on the GPU (other streams or threads) race on it,
- * so serialise them.  Particles with invalid data contribute nothing, and no
- * status word reports them.  Returns RAD_OK once the work is enqueued,
- * RAD_EINVAL for bad arguments, or RAD_ECUDA if the set-up or a launch failed. */
+ * so serialise them.  Returns RAD_OK once the work is enqueued, RAD_EINVAL for
+ * bad host-side arguments, or RAD_ECUDA if the set-up or a launch failed.
+ * What the device finds is reported by rad_static_status: particles with
+ * invalid data contribute nothing; a frequency or direction that is not finite
+ * and positive (non-zero) makes the whole step a no-op, leaving `state` as it
+ * was; a bounded wait that gave up leaves the step partly added. */
 #define RAD_STATIC_MAX_OMEGA 4096
 #define RAD_STATIC_MAX_DIRS 4096
 #define RAD_STATIC_MAX_BINS 65536
@@ -391,6 +397,16 @@ rad_status rad_accumulate_static(const double* omega, int32_t n_omega, const dou
                                  int32_t n_dir, int64_t n, const double* r, const double* beta,
                                  const double* beta_dot, const double* w, double t, double dt,
                                  float* state, void* stream);
+/* rad_static_status - what the device reported for the latest
+ * rad_accumulate_static call with particles on the current device: RAD_OK,
+ * RAD_EDATA (some particles were invalid and skipped), RAD_EINVAL (a frequency
+ * or direction was invalid: the step was skipped), RAD_ETIMEOUT (a bounded
+ * wait gave up: the step is incomplete), RAD_ECUDA (a debug build's index
+ * check failed, or the read failed).  Reads 4 bytes of the scratch array on
+ * `stream` (NULL = legacy default stream) and synchronises that stream; it
+ * allocates nothing.  The word belongs to the shared array, so the answer is
+ * about whichever call ran last on this device. */
+rad_status rad_static_status(void* stream);
 
 /* Diagnostics. */
 const char* rad_status_str(rad_status s);

@@ -42,7 +42,10 @@ static_assert(kMinChunk % kChunkAlign == 0, "the minimum chunk is a whole number
 
 // Device status bits (per job).
 // ST_BOUNDS: an index check of a debug build (RAD_DEBUG_BOUNDS) failed.
-enum : int { ST_BAD_PARTICLE = 1, ST_SLOW_PHASE = 2, ST_TIMEOUT = 4, ST_BOUNDS = 8 };
+// ST_BAD_GRID: a frequency or direction given in device memory (the
+// allocation-free entry) was not finite and positive / non-zero; the step was
+// skipped.
+enum : int { ST_BAD_PARTICLE = 1, ST_SLOW_PHASE = 2, ST_TIMEOUT = 4, ST_BOUNDS = 8, ST_BAD_GRID = 16 };
 
 // Per-job data that does not change between calls.
 struct JobStatic {
@@ -65,6 +68,7 @@ struct JobStatic {
   int* status;
   // literal mode (RAD_FF_LITERAL): the paper's sum P with weights F_k(omega)
   int literal;
+  int skip;                       // 1: the grid is invalid, every particle weighs zero
   const float* f2_tab;            // [n_omega] f(omega)^2 of the creation shape
   float* state_p;                 // [8][n_bins]: P.e1, P.e2 re/im sums, then compensations
   float* partials_p;              // [chunk_cap][4][n_bins]

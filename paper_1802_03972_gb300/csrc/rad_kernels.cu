@@ -53,9 +53,10 @@ __global__ void __launch_bounds__(256) prepass_kernel(LaunchArgs a) {
   const double ax = K.bdot[k], ay = K.bdot[n + k], az = K.bdot[2 * n + k];
   const double w = K.w[k];
   const double g2 = 1.0 - (bx * bx + by * by + bz * bz);
-  const bool ok = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(bx) && isfinite(by) &&
-                  isfinite(bz) && isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(w) &&
-                  w > 0.0 && g2 > 0.0 && isfinite(K.dt) && isfinite(K.t);
+  const bool valid = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(bx) && isfinite(by) &&
+                     isfinite(bz) && isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(w) &&
+                     w > 0.0 && g2 > 0.0 && isfinite(K.dt) && isfinite(K.t);
+  const bool ok = valid && !J.skip;
   float v[kRecFields];
   if (ok) {
     dev::split_ff((x - rr[0]) * kInvC, v[0], v[3]);
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(256) prepass_kernel(LaunchArgs a) {
     v[17] = __double2float_rn(sqrt(w) * K.dt);
     v[18] = __double2float_rn(w - 1.0);
   } else {
-    atomicOr(J.status, ST_BAD_PARTICLE);
+    if (!valid) atomicOr(J.status, ST_BAD_PARTICLE);
 #pragma unroll
     for (int f = 0; f < 19; ++f) v[f] = 0.0f;
     v[8] = 0.5f;   // a harmless finite beta (zero weights)

@@ -71,6 +71,9 @@ __global__ void __launch_bounds__(1024) static_setup_kernel(const double* __rest
                                                             const double* __restrict__ dirs,
                                                             JobStatic js, unsigned char* base) {
   __shared__ float s_max[32];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
   float* om_tab = reinterpret_cast<float*>(base + kOffOmTab);
   double* om_turns = reinterpret_cast<double*>(base + kOffOmTurns);
   float* dir_tab = reinterpret_cast<float*>(base + kOffDirTab);
@@ -79,7 +82,13 @@ __global__ void __launch_bounds__(1024) static_setup_kernel(const double* __rest
   const int no = js.n_omega, ndir = js.n_dir;
   float mx = 0.0f;
   for (int i = threadIdx.x; i < no; i += blockDim.x) {
-    const double turns = omega[i] / kTwoPi;
+    double om = omega[i];
+    if (!(om > 0.0) || !isfinite(om)) {
+      // invalid: a harmless finite stand-in; the step is skipped (see below)
+      s_bad = 1;
+      om = 1.0;
+    }
+    const double turns = om / kTwoPi;
     const float hi = __double2float_rn(turns);
     const float lo = __double2float_rn(turns - (double)hi);
     om_turns[i] = turns;
@@ -91,7 +100,13 @@ __global__ void __launch_bounds__(1024) static_setup_kernel(const double* __rest
   for (int d = threadIdx.x; d < ndir; d += blockDim.x) {
     double n[3] = {dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2]};
     const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-    for (int i = 0; i < 3; ++i) n[i] /= len;
+    if (!(len > 0.0) || !isfinite(len)) {
+      s_bad = 1;
+      n[0] = n[1] = 0.0;
+      n[2] = 1.0;
+    } else {
+      for (int i = 0; i < 3; ++i) n[i] /= len;
+    }
     int ax = 0;
     if (fabs(n[1]) < fabs(n[ax])) ax = 1;
     if (fabs(n[2]) < fabs(n[ax])) ax = 2;
@@ -114,10 +129,6 @@ __global__ void __launch_bounds__(1024) static_setup_kernel(const double* __rest
   }
   // Calls share the array: clear what must start at zero.
   for (int i = threadIdx.x; i < js.n_tiles; i += blockDim.x) tile_cnt[i] = 0u;
-  if (threadIdx.x == 0) {
-    *reinterpret_cast<int*>(base + kOffStatus) = 0;
-    *reinterpret_cast<unsigned long long*>(base + kOffCounter) = 0ULL;
-  }
   for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
   __syncthreads();
@@ -125,7 +136,12 @@ __global__ void __launch_bounds__(1024) static_setup_kernel(const double* __rest
     float m = 0.0f;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, s_max[i]);
     js.tau_fast = (float)(2097152.0 / fmax((double)m, 1e-300));  // 2^21 turns
+    // An invalid grid skips the step: every particle then weighs zero, so the
+    // caller's accumulators keep their value, and the status word says why.
+    js.skip = s_bad;
     *reinterpret_cast<JobStatic*>(base + kOffJob) = js;
+    *reinterpret_cast<int*>(base + kOffStatus) = s_bad ? ST_BAD_GRID : 0;
+    *reinterpret_cast<unsigned long long*>(base + kOffCounter) = 0ULL;
   }
 }
 
@@ -202,5 +218,27 @@ extern "C" rad_status rad_accumulate_static(const double* omega, int32_t n_omega
   if (launch_prepass(a, (int)((n + 255) / 256), s) != cudaSuccess) return RAD_ECUDA;
   const long long grid = std::min<long long>(a.n_items, resident_ctas(variant));
   if (launch_accumulate(variant, a, (int)grid, s) != cudaSuccess) return RAD_ECUDA;
+  return RAD_OK;
+}
+
+// Status of the latest rad_accumulate_static call on this device: one 4-byte
+// read of the status word in the scratch array, in stream order.
+extern "C" rad_status rad_static_status(void* stream) {
+  unsigned char* base = nullptr;
+  if (scratch_base(&base) != cudaSuccess) return RAD_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = 0;
+  if (cudaMemcpyAsync(&st, base + kOffStatus, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return RAD_ECUDA;
+  if (st & ST_BOUNDS) {
+    rad_log(1, "an index check of the debug build failed in the allocation-free entry (status 0x%x)",
+            st);
+    return RAD_ECUDA;
+  }
+  if (st & ST_TIMEOUT) return RAD_ETIMEOUT;
+  if (st & ST_BAD_GRID) return RAD_EINVAL;
+  if (st & ST_BAD_PARTICLE) return RAD_EDATA;
   return RAD_OK;
 }

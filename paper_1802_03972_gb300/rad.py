@@ -35,6 +35,7 @@ EXPORTS = [
     "rad_job_finish", "rad_job_poll", "rad_job_result", "rad_server_stats_get",
     "rad_server_destroy", "rad_status_str", "rad_last_error", "rad_kernel_launch_count",
     "rad_probe_peaks", "rad_probe_tensor", "rad_profile_enable", "rad_profile_read", "rad_profile_clock", "rad_accumulate_static",
+    "rad_static_status",
     "rad_spectrum_literal", "rad_push_step", "rad_push_flush",
     "rad_selftest_wait", "rad_selftest_stage1", "rad_selftest_phase",
 ]
@@ -135,6 +136,7 @@ def load(path: str = LIB_PATH):
         "rad_selftest_stage1": (st, [vp, i64, vp, vp, vp, vp, dbl, dbl, i32, vp, vp]),
         "rad_selftest_phase": (st, [vp, i32, vp, vp, vp, vp]),
         "rad_accumulate_static": (st, [vp, i32, vp, i32, i64, vp, vp, vp, vp, dbl, dbl, vp, vp]),
+        "rad_static_status": (st, [vp]),
         "rad_spectrum_literal": (st, [vp, vp]),
         "rad_push_step": (st, [vp, i64, vp, vp, vp, dbl, dbl]),
         "rad_push_flush": (st, [vp]),
@@ -401,6 +403,13 @@ def accumulate_static(omega, dirs, r, beta, beta_dot, w, t: float, dt: float, st
                                         _ptr(beta), _ptr(beta_dot), _ptr(w), float(t), float(dt),
                                         _ptr(state), _stream_handle(stream)),
            "rad_accumulate_static")
+
+
+def static_status(stream=None) -> int:
+    """rad_static_status: the device's report on the latest accumulate_static call
+    on the current device, as a status code (RAD_OK, RAD_EDATA, RAD_EINVAL,
+    RAD_ETIMEOUT, RAD_ECUDA); synchronises the stream."""
+    return int(load().rad_static_status(_stream_handle(stream)))
 
 
 def make_step(n, r, beta, beta_dot, w, t, dt) -> rad_step:

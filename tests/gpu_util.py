@@ -9,6 +9,17 @@ from paper_1802_03972_gb300 import inputs
 
 TOL_TOTAL = 1e-5   # relative spectral error of the mixed path vs the FP64 oracle
 TOL_FP64 = 1e-9    # plain FP64 kernel vs the oracle (different summation order only)
+# Per-bin gate (every bin of every direction, each part separately):
+#   |I - I_ref| <= BIN_REL I_ref + 2 BIN_AMP sqrt(I_ref M) + BIN_AMP^2 M,
+# M = the direction's largest I_ref.  It is the intensity error of an amplitude
+# S' = S (1 + e_r) + e_a with |e_r| <= BIN_REL / 2 (rounding of the bin's own sum)
+# and |e_a| <= BIN_AMP |S_max| (errors of single terms -- sin/cos, the TF32
+# split, the FP32 phase -- on sums whose scale is set by the direction's
+# largest amplitude).  Bins far below their direction's peak get a relative
+# bound that grows like sqrt(M / I_ref), as amplitude errors of that size must;
+# a spectral null (I_ref = 0 with M = 0) must be matched exactly.
+BIN_REL, BIN_AMP = 1e-5, 2e-6
+BIN_REL_FP64, BIN_AMP_FP64 = 1e-9, 1e-10
 
 
 def row_error(got, ref) -> float:
@@ -23,6 +34,32 @@ def row_error(got, ref) -> float:
             continue
         err = max(err, np.linalg.norm(g - r) / nr)
     return err
+
+
+def bin_excess(got, ref, rel: float = BIN_REL, amp: float = BIN_AMP) -> float:
+    """Largest ratio over all bins of |I - I_ref| to the per-bin allowance (see
+    BIN_REL, BIN_AMP); the gate passes when it is <= 1.  Rows are directions."""
+    ref = np.asarray(ref, dtype=np.float64)
+    ref2 = ref.reshape(ref.shape[0], -1) if ref.ndim > 1 else ref.reshape(1, -1)
+    got2 = np.asarray(got, dtype=np.float64).reshape(ref2.shape)
+    m = np.abs(ref2).max(axis=1, keepdims=True)
+    allowed = rel * np.abs(ref2) + 2.0 * amp * np.sqrt(np.abs(ref2) * m) + amp * amp * m
+    diff = np.abs(got2 - ref2)
+    if not np.all(np.isfinite(got2)):
+        return float("inf")
+    zero = allowed == 0.0
+    if np.any(diff[zero] != 0.0):
+        return float("inf")
+    return float(np.max(np.where(zero, 0.0, diff / np.where(zero, 1.0, allowed)), initial=0.0))
+
+
+def assert_parity(got, ref, tol: float = TOL_TOTAL, what: str = "", fp64: bool = False) -> dict:
+    """The two parity gates: per-direction 2-norm error <= tol, and every bin
+    within its per-bin allowance.  Returns both figures."""
+    row = row_error(got, ref)
+    ex = bin_excess(got, ref, *((BIN_REL_FP64, BIN_AMP_FP64) if fp64 else (BIN_REL, BIN_AMP)))
+    assert row <= tol and ex <= 1.0, f"{what}: row error {row:.3e} (gate {tol:g}), bin excess {ex:.3f}"
+    return {"row": row, "bin_excess": ex}
 
 
 def to_dev(a):

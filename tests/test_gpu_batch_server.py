@@ -5,7 +5,7 @@ import time
 import numpy as np
 import pytest
 
-from gpu_util import TOL_TOTAL, gpu_run, oracle_run, row_error, spectra_grid, to_dev
+from gpu_util import assert_parity, gpu_run, oracle_run, spectra_grid, to_dev
 from paper_1802_03972_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -50,7 +50,7 @@ def test_batch_equals_standalone_bitwise_and_oracle():
         for x, y in zip(a.spectrum(), c.spectrum()):
             np.testing.assert_array_equal(x, y)
         ref = spectra_grid(oracle_run(wl, range(6)), wl)
-        assert row_error(c.spectrum()[2], ref["tot"]) <= TOL_TOTAL
+        assert_parity(c.spectrum()[2], ref["tot"])
 
 
 def test_batch_graph_replay_with_fixed_buffers():
@@ -104,7 +104,7 @@ def test_checkpoint_resume_and_merge():
             ranks[k].accumulate(to_dev(r), to_dev(b_), to_dev(bd), to_dev(st.w[sl]), st.t, st.dt)
     ranks[0].state_merge(ranks[1].state_export())
     ref = spectra_grid(oracle_run(wl, range(8)), wl)
-    assert row_error(ranks[0].spectrum()[2], ref["tot"]) <= TOL_TOTAL
+    assert_parity(ranks[0].spectrum()[2], ref["tot"])
     with pytest.raises(rad.RadError):
         other = rad.Context(wl.omega[:32], wl.dirs, wl.ff_kind, wl.ff_width)
         other.state_import(blob)
@@ -117,7 +117,7 @@ def test_tune_keeps_parity():
     assert tile[0] in (0, 1, 2, 3, 4, 5, 7, 8)  # 6 is the literal sum's own variant
     gpu_run(wl, range(5), ctx=ctx)
     ref = spectra_grid(oracle_run(wl, range(5)), wl)
-    assert row_error(ctx.spectrum()[2], ref["tot"]) <= TOL_TOTAL
+    assert_parity(ctx.spectrum()[2], ref["tot"])
 
 
 @pytest.mark.parametrize("policy", [(0, 0), (1, 1), (2, 1_000_000), (3, 1_000_000)])

@@ -8,7 +8,7 @@ import subprocess
 import numpy as np
 import pytest
 
-from gpu_util import TOL_TOTAL, oracle_run, row_error, spectra_grid
+from gpu_util import assert_parity, oracle_run, spectra_grid
 from paper_1802_03972_gb300 import inputs
 from test_abi_cpu import build_c_client
 
@@ -49,7 +49,7 @@ def test_c_client_matches_oracle_and_binding(tmp_path):
     got = np.fromfile(out, dtype=np.float64).reshape(3, wl.dirs.shape[0], wl.omega.size)
     ref = spectra_grid(oracle_run(wl, steps), wl)
     for k, g in zip(("coh", "inc", "tot"), got):
-        assert row_error(g, ref[k]) <= TOL_TOTAL, k
+        assert_parity(g, ref[k], what=k)
     ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
     for s in steps:
         st = wl.step(s)

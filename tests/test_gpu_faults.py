@@ -14,7 +14,7 @@ import time
 import numpy as np
 import pytest
 
-from gpu_util import TOL_TOTAL, gpu_run, oracle_run, row_error, spectra_grid, to_dev
+from gpu_util import assert_parity, gpu_run, oracle_run, spectra_grid, to_dev
 from paper_1802_03972_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -66,7 +66,7 @@ def test_bad_job_in_a_batch():
         ctxs[1].spectrum()
     assert ei.value.status == rad.RAD_EDATA
     ref = spectra_grid(oracle_run(wls[1], range(4)), wls[1])  # the valid particles only
-    assert row_error(ctxs[1].spectrum()[2], ref["tot"]) <= TOL_TOTAL  # reported once
+    assert_parity(ctxs[1].spectrum()[2], ref["tot"])  # reported once
 
 
 def test_bad_job_in_a_served_mix():
@@ -112,7 +112,7 @@ def test_bad_job_result_keeps_its_valid_spectrum():
     srv.finish(jid)
     tot = srv.result(jid, wl.dirs.shape[0], wl.omega.shape[0], timeout=120, accept_edata=True)[2]
     ref = spectra_grid(oracle_run(wl, range(4)), wl)
-    assert row_error(tot, ref["tot"]) <= TOL_TOTAL
+    assert_parity(tot, ref["tot"])
     srv.close()
 
 
@@ -131,7 +131,7 @@ def test_server_shutdown_with_jobs_in_flight():
     # the device is still usable
     ctx = gpu_run(wls[2], range(2))
     ref = spectra_grid(oracle_run(wls[2], range(2)), wls[2])
-    assert row_error(ctx.spectrum()[2], ref["tot"]) <= TOL_TOTAL
+    assert_parity(ctx.spectrum()[2], ref["tot"])
 
 
 def test_bounded_wait_gives_up_and_the_context_keeps_working():
@@ -142,4 +142,4 @@ def test_bounded_wait_gives_up_and_the_context_keeps_working():
     assert 0.045 <= waited <= 5.0, waited
     gpu_run(wl, range(2, 4), ctx=ctx)
     ref = spectra_grid(oracle_run(wl, range(4)), wl)
-    assert row_error(ctx.spectrum()[2], ref["tot"]) <= TOL_TOTAL
+    assert_parity(ctx.spectrum()[2], ref["tot"])

@@ -3,14 +3,15 @@ chunks of 1e6 into one time step, 1024 log frequencies x 32 x 32 directions
 (1.05e13 amplitude updates), read out with CIC and TSC shapes of 0.1 um.
 
 Checks: chunked streaming equals a different chunking (linearity of the sum),
-sampled bins equal the FP64 oracle within 1e-5 of their direction's RMS
-intensity, and the mixed-precision kernel equals the plain FP64 kernel on a
-reduced grid with all 1e7 particles."""
+32 sampled bins equal the FP64 oracle within the per-bin allowance of the
+other parity tests (the direction's largest intensity, which the per-bin gate
+scales with, taken from the GPU's row), and the mixed-precision kernel equals
+the plain FP64 kernel on a reduced grid with all 1e7 particles."""
 import numpy as np
 import pytest
 
 import oracle
-from gpu_util import TOL_TOTAL, row_error, to_dev
+from gpu_util import BIN_AMP, BIN_REL, assert_parity, to_dev
 from paper_1802_03972_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -58,10 +59,10 @@ def test_insitu_scale_chunked_sampled_and_shapes(bunch):
     ctx3 = rad.Context(omega, dirs, rad.FF_CIC, 0.1e-6)
     feed(ctx3, bunch, split=2)
     for a, b in zip(cic, ctx3.spectrum()):
-        assert row_error(b, a) <= TOL_TOTAL
+        assert_parity(b, a, what="chunking")
     # sampled bins against the oracle (all 1e7 particles)
     rng = np.random.default_rng(4)
-    bins = [(int(rng.integers(0, 1024)), int(rng.integers(0, 1024))) for _ in range(6)]
+    bins = [(int(rng.integers(0, 1024)), int(rng.integers(0, 1024))) for _ in range(32)]
     bo, bd = oracle.grid_bins(omega, dirs, bins)
     acc = oracle.Accumulator(bo, bd, oracle.FF_CIC, 0.1e-6)
     for st in bunch:
@@ -70,11 +71,10 @@ def test_insitu_scale_chunked_sampled_and_shapes(bunch):
         ref = acc.spectra(shape, 0.1e-6)
         for i, (d, o) in enumerate(bins):
             for k, g in zip(("coh", "inc", "tot"), got):
-                scale = np.sqrt(np.mean(g[d] ** 2))
-                if scale == 0.0:
-                    assert ref[k][i] == 0.0
-                    continue
-                assert abs(g[d, o] - ref[k][i]) <= TOL_TOTAL * scale, (shape, k, d, o)
+                m = np.abs(g[d]).max()
+                r = ref[k][i]
+                allowed = BIN_REL * r + 2.0 * BIN_AMP * np.sqrt(r * m) + BIN_AMP ** 2 * m
+                assert abs(g[d, o] - r) <= allowed, (shape, k, d, o, g[d, o], r)
 
 
 def test_insitu_scale_mixed_vs_plain_fp64(bunch):
@@ -85,4 +85,4 @@ def test_insitu_scale_mixed_vs_plain_fp64(bunch):
     feed(mixed, bunch)
     feed(plain, bunch)
     for a, b in zip(mixed.spectrum(), plain.spectrum()):
-        assert row_error(a, b) <= TOL_TOTAL
+        assert_parity(a, b, what="mixed vs plain FP64")

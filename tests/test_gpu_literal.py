@@ -3,7 +3,7 @@ F_k = sqrt(w + (w^2 - w) f^2) of Eq. 12) against the oracle's literal sum P."""
 import numpy as np
 import pytest
 
-from gpu_util import TOL_TOTAL, oracle_run, row_error, spectra_grid, to_dev
+from gpu_util import assert_parity, oracle_run, row_error, spectra_grid, to_dev
 import oracle
 from paper_1802_03972_gb300 import inputs
 
@@ -40,9 +40,9 @@ def test_literal_sum_matches_oracle_with_unequal_weights(kind, width):
     ref = spectra_grid(oracle_run(wl, range(6)), wl)
     ctx = run_literal(wl, range(6))
     lit = ctx.spectrum_literal()
-    assert row_error(lit, ref["paper"]) <= TOL_TOTAL
+    assert_parity(lit, ref["paper"], what="literal")
     coh, inc, tot = ctx.spectrum()
-    assert row_error(tot, ref["tot"]) <= TOL_TOTAL
+    assert_parity(tot, ref["tot"], what="tot")
     f2 = oracle.form_factor(kind, width, wl.omega) ** 2
     m = (f2 > 1e-6) & (f2 < 1e-2)
     assert m.sum() >= 3
@@ -58,7 +58,7 @@ def test_literal_equals_split_for_equal_weights():
     ctx = run_literal(wl, range(5))
     lit = ctx.spectrum_literal()
     tot = ctx.spectrum()[2]
-    assert row_error(lit, tot) <= TOL_TOTAL
+    assert_parity(lit, tot, what="literal vs split")
 
 
 def test_literal_checkpoint_and_restrictions():

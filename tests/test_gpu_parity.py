@@ -2,7 +2,9 @@
 
 Tolerances: relative spectral error per direction (2-norm over frequencies)
 <= 1e-5 for the mixed-precision path on the total spectrum and on its
-coherent and incoherent parts; <= 1e-9 for the plain FP64 kernel.
+coherent and incoherent parts, and every bin within the per-bin allowance of
+gpu_util (relative 1e-5 plus an amplitude error of 2e-6 of the direction's
+largest amplitude); 1e-9 (per bin: 1e-9 and 1e-10) for the plain FP64 kernel.
 """
 import math
 
@@ -10,7 +12,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import TOL_FP64, TOL_TOTAL, gpu_run, oracle_run, row_error, spectra_grid, to_dev
+from gpu_util import (TOL_FP64, TOL_TOTAL, assert_parity, gpu_run, oracle_run, spectra_grid,
+                      to_dev)
 from paper_1802_03972_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -30,8 +33,7 @@ def check(ctx, ref, tol=TOL_TOTAL, parts=("tot", "coh", "inc"), ff=None):
     got = {"coh": coh, "inc": inc, "tot": tot}
     errs = {}
     for k in parts:
-        errs[k] = row_error(got[k], ref[k])
-        assert errs[k] <= tol, (k, errs)
+        errs[k] = assert_parity(got[k], ref[k], tol, what=k, fp64=tol == TOL_FP64)
     return errs
 
 
@@ -137,7 +139,36 @@ def test_lwfa_full_size_sampled_rows():
     bins = [(d, o) for d in rows for o in range(512)]
     ref = {k: v.reshape(len(rows), 512) for k, v in oracle_run(wl, steps, bins).spectra().items()}
     for k, g in (("tot", tot), ("coh", coh), ("inc", inc)):
-        assert row_error(g[rows], ref[k]) <= TOL_TOTAL, k
+        assert_parity(g[rows], ref[k], what=k)
+
+
+def test_lwfa_full_size_256_steps():
+    """Accuracy over the workload's horizon: the full LWFA bunch for 256 of its
+    2048 steps in the benchmark's launch configuration (the tuned tile), read out
+    after 16, 64 and 256 steps.  This covers Eq. 13's sum over time in the
+    precision the kernel uses (per-call partial sums rotated by the reference
+    phase and added into compensated FP32 state).  The oracle computes 2
+    directions x all 512 frequencies; both gates hold at every readout, and the
+    error does not grow with the step count."""
+    wl = inputs.lwfa_bunch()
+    ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
+    ctx.tune(wl.n_particles)
+    rows = [5, 200]
+    n_om = wl.omega.shape[0]
+    acc = oracle_run(wl, [], [(d, o) for d in rows for o in range(n_om)])
+    errs = {}
+    for s in range(256):
+        st = wl.step(s)
+        ctx.accumulate(to_dev(st.r), to_dev(st.beta), to_dev(st.beta_dot), to_dev(st.w), st.t, st.dt)
+        acc.accumulate(st.r, st.beta, st.beta_dot, st.w, st.t, st.dt)
+        if s + 1 in (16, 64, 256):
+            got = dict(zip(("coh", "inc", "tot"), ctx.spectrum()))
+            ref = {k: v.reshape(len(rows), n_om) for k, v in acc.spectra().items()}
+            errs[s + 1] = {k: assert_parity(got[k][rows], ref[k], what=f"{k} after {s + 1} steps")
+                           for k in ("tot", "coh", "inc")}
+    # no drift: the error after 256 steps stays within 2x of the error after 16
+    assert errs[256]["tot"]["row"] <= 2.0 * errs[16]["tot"]["row"] + 1e-7, errs
+    ctx.close()
 
 
 def test_edge_cases_small_sizes():

@@ -4,7 +4,7 @@ analytic beta_dot of the trajectory."""
 import numpy as np
 import pytest
 
-from gpu_util import TOL_TOTAL, gpu_run, oracle_run, row_error, spectra_grid, to_dev
+from gpu_util import assert_parity, gpu_run, row_error, spectra_grid, to_dev
 import oracle
 from paper_1802_03972_gb300 import inputs
 
@@ -45,7 +45,7 @@ def test_push_matches_oracle_with_finite_differences():
     ctx.push_flush()
     coh, inc, tot = ctx.spectrum()
     for k, g in (("tot", tot), ("coh", coh), ("inc", inc)):
-        assert row_error(g, ref[k]) <= TOL_TOTAL, k
+        assert_parity(g, ref[k], what=k)
 
 
 def test_push_agrees_with_analytic_beta_dot():

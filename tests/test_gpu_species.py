@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import TOL_FP64, TOL_TOTAL, gpu_run, oracle_run, row_error, to_dev
+from gpu_util import TOL_FP64, TOL_TOTAL, assert_parity, gpu_run, oracle_run, row_error, to_dev
 from paper_1802_03972_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -63,7 +63,7 @@ def test_three_species_match_oracle(reference, prec):
     coh, inc, tot = rad.spectrum_species(ctxs, FFS)
     tol = TOL_TOTAL if prec == rad.PREC_MIXED else TOL_FP64
     for k, got in (("coh", coh), ("inc", inc), ("tot", tot)):
-        assert row_error(got, ref[k]) <= tol, (k, row_error(got, ref[k]))
+        assert_parity(got, ref[k], tol, what=k, fp64=prec != rad.PREC_MIXED)
     # device outputs give the same bytes as host outputs
     dev = tuple(torch.zeros(wls[0].dirs.shape[0], wls[0].omega.shape[0], dtype=torch.float64,
                             device="cuda") for _ in range(3))
@@ -132,4 +132,4 @@ def test_species_with_invalid_particles_reports_once_and_keeps_spectra():
     again = rad.spectrum_species([good, bad], FFS[:2])  # reported once: now clean
     for k, a, b2 in zip(("coh", "inc", "tot"), first, again):
         np.testing.assert_array_equal(a, b2)
-        assert row_error(a, ref[k]) <= TOL_TOTAL, k
+        assert_parity(a, ref[k], what=k)
