@@ -199,6 +199,20 @@ void rad_server::loop() {
     if (policy == RAD_SERVE_LEAST_SERVED)
       std::stable_sort(ready.begin(), ready.end(),
                        [](const Job* a, const Job* b) { return a->served < b->served; });
+    // Oldest job with bounded backfill: the oldest ready job always gets its
+    // step, and other jobs (least served first) join only while the round's
+    // work stays within max(round_updates, 17/16 of the head's step).  The head
+    // of the queue then runs at >= 16/17 of its own pace, as under FIFO, which
+    // keeps the tail latency of a FIFO queue, while small jobs progress in the
+    // margin instead of waiting behind large ones.
+    const bool backfill = policy == RAD_SERVE_OLDEST_BACKFILL;
+    long long budget = round_updates;
+    if (backfill && !ready.empty()) {
+      std::stable_sort(ready.begin() + 1, ready.end(),
+                       [](const Job* a, const Job* b) { return a->served < b->served; });
+      const long long head = ready[0]->queue.front().n * (long long)ready[0]->ctx->n_bins;
+      budget = std::max(round_updates, head + head / 16);
+    }
     if (policy == RAD_SERVE_LEAST_SERVED_AGED) {
       // Attained service minus a credit for the time since submission, at one
       // round's updates per 12 ms (about the GPU's rate): a job that has waited
@@ -221,9 +235,14 @@ void rad_server::loop() {
     long long round_work = 0;
     for (Job* jp : ready) {
       Job& j = *jp;
-      if (policy != RAD_SERVE_ALL && !in_round.empty() && round_work >= round_updates) break;
       QueuedStep& q = j.queue.front();
-      round_work += q.n * (long long)j.ctx->n_bins;
+      const long long work = q.n * (long long)j.ctx->n_bins;
+      if (backfill) {
+        if (!in_round.empty() && round_work + work > budget) continue;
+      } else if (policy != RAD_SERVE_ALL && !in_round.empty() && round_work >= round_updates) {
+        break;
+      }
+      round_work += work;
       Slot& sl = j.slots[q.slot];
       const long long n = q.n;
       rad_step s;
@@ -339,7 +358,7 @@ rad_status rad_server_create(size_t hbm_budget, int32_t max_slots, void* stream,
 }
 
 rad_status rad_server_set_policy(rad_server* s, int32_t policy, int64_t round_updates) {
-  if (!s || policy < RAD_SERVE_ALL || policy > RAD_SERVE_LEAST_SERVED_AGED) return RAD_EINVAL;
+  if (!s || policy < RAD_SERVE_ALL || policy > RAD_SERVE_OLDEST_BACKFILL) return RAD_EINVAL;
   if (policy != RAD_SERVE_ALL && round_updates < 1) return RAD_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
   s->policy = policy;

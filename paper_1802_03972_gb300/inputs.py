@@ -216,16 +216,18 @@ class JobSpec:
 
 
 def job_mix(n_jobs: int = 64, base_seed: int = 4000, n_lo: float = 1e3, n_hi: float = 1e6,
-            steps: tuple = (200, 200)) -> list[JobSpec]:
-    """Batched-jobs mix: N log-uniform in [1e3, 1e6], omega grids 64..1024
-    (powers of two), square direction grids 4^2..32^2, gamma log-uniform in
-    [50, 1000] (each job's bunch), sigma uniform in [0.5, 5] um."""
+            steps: tuple = (200, 200), log2_omega: tuple = (6, 10),
+            log2_side: tuple = (2, 5)) -> list[JobSpec]:
+    """Batched-jobs mix: N log-uniform in [n_lo, n_hi] (default 1e3..1e6), omega
+    grids 2^6..2^10 = 64..1024 and square direction grids (2^2)^2..(2^5)^2 =
+    4^2..32^2 by default (powers of two, inclusive ranges of exponents), gamma
+    log-uniform in [50, 1000] (each job's bunch), sigma uniform in [0.5, 5] um."""
     out = []
     for j in range(n_jobs):
         rng = np.random.Generator(np.random.PCG64(base_seed + j))
         n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
-        n_omega = int(2 ** rng.integers(6, 11))
-        n_side = int(2 ** rng.integers(2, 6))
+        n_omega = int(2 ** rng.integers(log2_omega[0], log2_omega[1] + 1))
+        n_side = int(2 ** rng.integers(log2_side[0], log2_side[1] + 1))
         g = math.exp(rng.uniform(math.log(50.0), math.log(1000.0)))
         sigma = rng.uniform(0.5e-6, 5e-6)
         n_steps = int(rng.integers(steps[0], steps[1] + 1))

@@ -42,6 +42,7 @@ EXPORTS = [
 FF_LITERAL = 2  # rad_ff.flags at creation: also accumulate the paper's literal sum
 # Round policies of the serving loop (rad_server_set_policy).
 SERVE_ALL, SERVE_OLDEST, SERVE_LEAST_SERVED, SERVE_LEAST_SERVED_AGED = 0, 1, 2, 3
+SERVE_OLDEST_BACKFILL = 4
 
 # Limits of rad_accumulate_static (include/rad.h).
 STATIC_MAX_OMEGA, STATIC_MAX_DIRS, STATIC_MAX_BINS, STATIC_MAX_PARTICLES = 4096, 4096, 65536, 65536

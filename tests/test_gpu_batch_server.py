@@ -120,12 +120,13 @@ def test_tune_keeps_parity():
     assert_parity(ctx.spectrum()[2], ref["tot"])
 
 
-@pytest.mark.parametrize("policy", [(0, 0), (1, 1), (2, 1_000_000), (3, 1_000_000)])
+@pytest.mark.parametrize("policy", [(0, 0), (1, 1), (2, 1_000_000), (3, 1_000_000), (4, 1_000_000)])
 def test_server_results_equal_alone_and_in_the_mix(policy):
     """Jobs submitted at different times, steps fed incrementally, one slot fewer
     than jobs (admission waits); each result equals the standalone run, under
     every round policy (all ready jobs; one job per round in arrival order; least
-    served first up to 1e6 updates per round)."""
+    served first up to 1e6 updates per round, with and without aging; the oldest
+    job with bounded backfill)."""
     wls = small_jobs()
     srv = rad.Server(hbm_budget=8 << 30, max_slots=3)
     srv.set_policy(*policy)
@@ -161,7 +162,7 @@ def test_server_results_equal_alone_and_in_the_mix(policy):
 
 def test_server_policy_arguments():
     srv = rad.Server(hbm_budget=1 << 30, max_slots=2)
-    for bad in ((4, 10), (-1, 10), (1, 0), (2, -5), (3, 0)):
+    for bad in ((5, 10), (-1, 10), (1, 0), (2, -5), (3, 0), (4, 0)):
         with pytest.raises(rad.RadError):
             srv.set_policy(*bad)
     srv.set_policy(rad.SERVE_ALL, 0)
