@@ -303,6 +303,46 @@ def modes_leg(wl, ring_dev, steps_host, upd: int, n_steps: int = 20):
     return out
 
 
+def wide_leg(wl, tile, n_steps: int = 10):
+    """The headline workload's grids with its bunch stretched to 2 mm along z
+    (z uniform over +-1 mm, the rest as generated): about 50 times the fast
+    phase range about one reference point, as when one call holds a whole
+    domain (Sec. 3.3).  The call is sorted and its tiles rotated per group;
+    timed like the headline, in the same tile."""
+    import numpy as np
+    import torch
+
+    from paper_1802_03972_gb300 import rad
+    rng = np.random.default_rng(12)
+    n = wl.n_particles
+    ring = []
+    for s in range(n_steps):
+        st = wl.step(s)
+        r = st.r.reshape(3, n).copy()
+        r[2] = rng.uniform(-1e-3, 1e-3, n) + 299792458.0 * st.t
+        ring.append(([torch.from_numpy(np.ascontiguousarray(a)).cuda()
+                      for a in (r.ravel(), st.beta, st.beta_dot, st.w)], st.t, st.dt))
+    ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
+    ctx.set_tile(*tile)
+    ctx.accumulate(*ring[0][0], ring[0][1], ring[0][2])
+    ctx.sync()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for d, t_, dt in ring:
+        ctx.accumulate(*d, t_, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    pre_ms, acc_ms, calls = ctx.profile_read()
+    el = e0.elapsed_time(e1) / 1e3
+    ctx.close()
+    upd = wl.updates_per_step()
+    return {"workload": "headline grids, 1e5 macro-particles with z uniform over +-1 mm",
+            "value": n_steps * upd / el, "unit": UNIT, "steps": n_steps, "tile": list(tile),
+            "prepass_and_sort_ms_per_step": pre_ms / max(calls, 1),
+            "accumulate_ms_per_step": acc_ms / max(calls, 1)}
+
+
 def batch_leg(rounds: int, n_jobs: int = 64, specs=None, mix: str = "batched job mix"):
     """n_jobs independent jobs (default: the batched job mix) advanced one step per
     round in one persistent launch, CUDA-graph replayed; against the same jobs
@@ -852,6 +892,8 @@ def main():
     modes = None
     if rank == 0 and not args.no_modes:
         modes = modes_leg(wl, ring_dev, steps_host, upd)
+        modes["wide_bunch"] = wide_leg(wl, ctx.get_tile())
+        modes["wide_bunch"]["over_headline"] = modes["wide_bunch"]["value"] / (value / world)
 
     insitu = None
     if rank == 0 and not args.no_insitu:

@@ -202,6 +202,14 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
+// Reference time of a wide call's particle group (the group holding particle
+// kt) seen from direction d: -n . (r_group - r_ref) / c.
+__device__ __forceinline__ double group_tau(const JobStatic& J, long long kt, int d) {
+  const double* D = J.gref + 3 * (kt / kGroup);
+  const double* nd = J.dirs + 3 * d;
+  return -(nd[0] * D[0] + nd[1] * D[1] + nd[2] * D[2]) * kInvC;
+}
+
 // Loads one raw particle tile; thread 0 only.
 __device__ __forceinline__ void issue_tile(const JobStatic& J, long long k0, int KT, float* raw,
                                            uint64_t* bar) {
@@ -213,7 +221,7 @@ __device__ __forceinline__ void issue_tile(const JobStatic& J, long long k0, int
 // ------------------------------------------------------------ FP32 variant
 // LIT: also the paper's literal sum P_i += sqrt(w) dt a_i g e^{i phi} with
 // g = sqrt(1 + (w - 1) f(omega)^2), i.e. F_k(omega) dt a_i (Eq. 13 with Eq. 12).
-template <int THREADS, int W, int UNROLL, bool LIT = false>
+template <int THREADS, int W, int UNROLL, bool LIT = false, bool WIDE = false>
 __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCall& K, int tile,
                                                  int chunk, unsigned char* __restrict__ smem,
                                                  uint64_t* bar, uint32_t& phase, int* s_flag) {
@@ -231,6 +239,8 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
   const int n_om = J.n_omega;
   const int s1_dl = threadIdx.x / g.KT, s1_kk = threadIdx.x - s1_dl * g.KT;
   const int s1_d = min(g.d0 + s1_dl, J.n_dir - 1);
+  // WIDE: a wide call, whose records are relative to their group's reference point.
+  constexpr bool wide = WIDE;
 
   float2 omh[NP], wh[NP], wl[NP];
 #pragma unroll
@@ -337,6 +347,8 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
       // Wide path: some |dtau| exceed the fast range in this tile; the phase of
       // every update is formed in FP64.
       if (threadIdx.x == 0) atomicOr(J.status, ST_SLOW_PHASE);
+      double tau_g = 0.0;
+      if constexpr (wide) tau_g = group_tau(J, kt, my_d);
       double omt[W];
 #pragma unroll
       for (int i = 0; i < W; ++i) omt[i] = J.om_turns[min(om_first + i, n_om - 1)];
@@ -346,8 +358,8 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
         const float4 r2 = rc[kk * g.NT * REC + 2];
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
-          const float2 ph = make_float2(phase_wide(omt[2 * p], r0.x, r0.z),
-                                        phase_wide(omt[2 * p + 1], r0.x, r0.z));
+          const float2 ph = make_float2(phase_wide(omt[2 * p], r0.x, r0.z, tau_g),
+                                        phase_wide(omt[2 * p + 1], r0.x, r0.z, tau_g));
           const float2 cc = make_float2(cos_approx(ph.x), cos_approx(ph.y));
           const float2 ss = make_float2(sin_approx(ph.x), sin_approx(ph.y));
           acc1[p][0] = __ffma2_rn(make_float2(r1.x, r1.y), cc, acc1[p][0]);
@@ -370,6 +382,26 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
             acc1[p][NC - 1] = __ffma2_rn(pv2, ss, acc1[p][NC - 1]);
           }
         }
+      }
+    }
+    // Wide call, fast path: the tile's sums are relative to its group's
+    // reference; rotate them by e^{i omega tau_g} (the FP64 path above already
+    // has tau_g in every phase).
+    if constexpr (wide) {
+      if (!(flags & 1)) {
+      const double tau_g = group_tau(J, kt, my_d);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        float2 cs, sn;
+        group_rotation(J.om_turns[min(om_first + 2 * p, n_om - 1)], tau_g, cs.x, sn.x);
+        group_rotation(J.om_turns[min(om_first + 2 * p + 1, n_om - 1)], tau_g, cs.y, sn.y);
+#pragma unroll
+        for (int c = 0; c < NC; c += 2) {
+          const float2 re = acc1[p][c], im = acc1[p][c + 1];
+          acc1[p][c] = __ffma2_rn(re, cs, __fmul2_rn(make_float2(-im.x, -im.y), sn));
+          acc1[p][c + 1] = __ffma2_rn(re, sn, __fmul2_rn(im, cs));
+        }
+      }
       }
     }
     // Two-level summation: the tile's sums join the chunk sums.
@@ -453,7 +485,7 @@ __device__ __forceinline__ void tc_block(float2 pA, float2 pB, uint32_t b0, uint
 
 // Warp layout: warp w handles direction d0 + w / (WT/32) and 32 frequencies
 // (two 16-row MMA blocks) starting at o0 + 32 (w % (WT/32)).
-template <int THREADS, int PASSES, int NB>
+template <int THREADS, int PASSES, int NB, bool WIDE = false>
 __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCall& K, int tile,
                                                 int chunk, unsigned char* __restrict__ smem,
                                                 uint64_t* bar, uint32_t& phase, int* s_flag) {
@@ -475,6 +507,8 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
   const int n_om = J.n_omega;
   const int s1_dl = threadIdx.x / g.KT, s1_kk = threadIdx.x - s1_dl * g.KT;
   const int s1_d = min(g.d0 + s1_dl, J.n_dir - 1);
+  // WIDE: a wide call, whose records are relative to their group's reference point.
+  constexpr bool wide = WIDE;
 
   float2 omh[NB], wh[NB], wl[NB];
   auto load_omega = [&](int o_warp) {
@@ -568,6 +602,8 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
         else fast_loop(kn8);
       } else {
         if (threadIdx.x == 0) atomicOr(J.status, ST_SLOW_PHASE);
+        double tau_g = 0.0;
+        if constexpr (wide) tau_g = group_tau(J, kt, my_d);
         double omt[NB][2];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -580,10 +616,40 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
           const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
-            const float2 pA = make_float2(phase_wide(omt[b][0], tA.x, tA.y), phase_wide(omt[b][1], tA.x, tA.y));
-            const float2 pB = make_float2(phase_wide(omt[b][0], tB.x, tB.y), phase_wide(omt[b][1], tB.x, tB.y));
+            const float2 pA = make_float2(phase_wide(omt[b][0], tA.x, tA.y, tau_g),
+                                          phase_wide(omt[b][1], tA.x, tA.y, tau_g));
+            const float2 pB = make_float2(phase_wide(omt[b][0], tB.x, tB.y, tau_g),
+                                          phase_wide(omt[b][1], tB.x, tB.y, tau_g));
             tc_block(pA, pB, b0, b1, dre[b], dim[b]);
           }
+        }
+      }
+      // Wide call, fast path: rotate the tile's sums by e^{i omega tau_g}.  The
+      // warp's 16 NB frequencies are shared out: lane L reduces the phases of
+      // frequencies L and L + 32 of the warp's range in FP64 (FP64 is narrow on
+      // this GPU), and each lane takes the factors of its rows r and r + 8 of
+      // every block from their owners by shuffles.
+      if constexpr (wide) {
+        if (!(flags & 1)) {
+          const double tau_g = group_tau(J, kt, my_d);
+          float cA, sA, cB = 1.0f, sB = 0.0f;
+          group_rotation(J.om_turns[min(o_warp + lane, n_om - 1)], tau_g, cA, sA);
+          if constexpr (NB > 2)
+            group_rotation(J.om_turns[min(o_warp + lane + 32, n_om - 1)], tau_g, cB, sB);
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int src = (16 * b + r + 8 * h) & 31;
+              const float cs = __shfl_sync(0xffffffffu, b < 2 ? cA : cB, src);
+              const float sn = __shfl_sync(0xffffffffu, b < 2 ? sA : sB, src);
+#pragma unroll
+              for (int e = 2 * h; e < 2 * h + 2; ++e) {
+                const float re = dre[b][e], im = dim[b][e];
+                dre[b][e] = fmaf(re, cs, -im * sn);
+                dim[b][e] = fmaf(re, sn, im * cs);
+              }
+            }
         }
       }
       float4* l2p = l2 + ps * GQ * THREADS + threadIdx.x;
@@ -630,8 +696,13 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
   return true;
 }
 
-template <int THREADS, int W, int MINB, bool TC, bool LIT, int PASSES = 1>
+// WIDE = false: the work items of jobs whose call is not wide; true: those of
+// wide calls (exits at once when no job of the launch is wide).  The two run
+// one after the other on the same stream, each with its own item counter, so
+// the common path keeps its register allocation free of the wide-call code.
+template <int THREADS, int W, int MINB, bool TC, bool LIT, int PASSES = 1, bool WIDE = false>
 __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a) {
+  if (WIDE && (a.any_wide == nullptr || *a.any_wide == 0)) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ long long s_item[2];
@@ -652,13 +723,14 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
   uint32_t phase = 0u;
   int buf = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_item[buf] = (long long)atomicAdd(a.item_counter, 1ULL);
+    if (threadIdx.x == 0) s_item[buf] = (long long)atomicAdd(a.item_counter + (WIDE ? 1 : 0), 1ULL);
     __syncthreads();
     const long long item = s_item[buf];
     buf ^= 1;
     if (item >= a.n_items) break;
     const int j = find_job(a, item);
     const JobStatic& J = a.js[j];
+    if ((J.wide_flag != nullptr && *J.wide_flag != 0) != WIDE) continue;  // the other kernel's
     const JobCall K = a.use_inline ? a.inline_call : a.jc[j];
     const long long local = item - K.item_begin;
     // Tile-major order: the chunks of one tile run close together in time, so
@@ -667,8 +739,11 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     const int tile = (int)(local / K.n_chunks);
     bool ok;
     if constexpr (TC)
-      ok = process_item_tc<THREADS, PASSES, 2 * W>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
-    else ok = process_item_fma<THREADS, W, 8, LIT>(J, K, tile, chunk, smem, &bar, phase, &s_flag);
+      ok = process_item_tc<THREADS, PASSES, 2 * W, WIDE>(J, K, tile, chunk, smem, &bar, phase,
+                                                         &s_flag);
+    else
+      ok = process_item_fma<THREADS, W, 8, LIT, WIDE>(J, K, tile, chunk, smem, &bar, phase,
+                                                      &s_flag);
     if (!ok) break;
   }
   if (a.prof_clk && threadIdx.x == 0) {
@@ -684,13 +759,20 @@ cudaError_t launch_acc(const LaunchArgs& a, int grid, cudaStream_t s) {
   static std::atomic<bool> attr_set[kMaxDevices];
   const int dev = current_device();
   if (dev < 0 || dev >= kMaxDevices || !attr_set[dev].load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P>,
+    cudaError_t e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < kMaxDevices) attr_set[dev].store(true, std::memory_order_release);
   }
-  accumulate_kernel<T, W, MINB, TC, LIT, P><<<grid, T, smem, s>>>(a);
+  accumulate_kernel<T, W, MINB, TC, LIT, P, false><<<grid, T, smem, s>>>(a);
   count_launches(1);
+  if (a.any_wide != nullptr) {
+    accumulate_kernel<T, W, MINB, TC, LIT, P, true><<<grid, T, smem, s>>>(a);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
@@ -698,9 +780,9 @@ template <int T, int W, int MINB, bool TC, bool LIT, int P = 1>
 int blocks_per_sm() {
   int nb = 0;
   const size_t smem = Smem<T, TC, LIT, TC ? P * W : P>::bytes;
-  cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P>,
+  cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P, false>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accumulate_kernel<T, W, MINB, TC, LIT, P>, T,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accumulate_kernel<T, W, MINB, TC, LIT, P, false>, T,
                                                     smem) != cudaSuccess ||
       nb < 1)
     nb = 1;

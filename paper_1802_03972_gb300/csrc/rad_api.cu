@@ -177,17 +177,29 @@ rad_status ensure_capacity(rad_ctx* c, long long n, int n_chunks) {
   if (n > c->h_js.n_cap) {
     long long cap = std::max(n, c->h_js.n_cap * 3 / 2);
     cap = (cap + 255) / 256 * 256;
-    if (c->h_js.rec) {
-      cudaStreamSynchronize(c->stream);
-      cudaFree(c->h_js.rec);
-      c->h_js.rec = nullptr;
+    JobStatic& js = c->h_js;
+    if (js.rec) cudaStreamSynchronize(c->stream);
+    void* old[] = {js.rec, js.perm, js.sort_counts, js.bucket_base, js.gref};
+    for (void* p : old)
+      if (p) cudaFree(p);
+    js.rec = nullptr;
+    js.perm = js.sort_counts = js.bucket_base = nullptr;
+    js.gref = nullptr;
+    // the record buffer, and the sort buffers of wide calls (12 B per particle)
+    rad_status s = cuda_check(c, dmalloc(&js.rec, (size_t)cap * kRecFields));
+    if (s == RAD_OK && js.wide_flag) {
+      s = cuda_check(c, dmalloc(&js.perm, (size_t)cap));
+      if (s == RAD_OK)
+        s = cuda_check(c, dmalloc(&js.sort_counts,
+                                  (size_t)((cap + kSortBlock - 1) / kSortBlock) * kSortBuckets));
+      if (s == RAD_OK) s = cuda_check(c, dmalloc(&js.bucket_base, (size_t)kSortBuckets));
+      if (s == RAD_OK) s = cuda_check(c, dmalloc(&js.gref, (size_t)3 * ((cap + kGroup - 1) / kGroup)));
     }
-    rad_status s = cuda_check(c, dmalloc(&c->h_js.rec, (size_t)cap * kRecFields));
     if (s != RAD_OK) {
-      c->h_js.n_cap = 0;
+      js.n_cap = 0;
       return s;
     }
-    c->h_js.n_cap = cap;
+    js.n_cap = cap;
     changed = true;
   }
   if (n_chunks > c->h_js.chunk_cap) {
@@ -288,7 +300,8 @@ rad_status enqueue_accumulate(rad_ctx* c, long long n, const double* r, const do
   a.n_jobs = 1;
   a.use_inline = 1;
   a.n_items = (long long)c->h_js.n_tiles * n_chunks;
-  a.item_counter = c->d_counter;
+  a.item_counter = c->d_counter;  // [0], [1]: item counters; [2]: the wide flag
+  a.any_wide = c->h_js.wide_flag;
   JobCall& K = a.inline_call;
   K.n = n;
   K.r = r;
@@ -301,7 +314,8 @@ rad_status enqueue_accumulate(rad_ctx* c, long long n, const double* r, const do
   K.n_chunks = n_chunks;
   K.item_begin = 0;
   K.block_begin = 0;
-  s = cuda_check(c, cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream));
+  s = cuda_check(c, cudaMemsetAsync(c->d_counter, 0, kCounterWords * sizeof(unsigned long long),
+                                    c->stream));
   if (s != RAD_OK) return s;
   cudaEvent_t* ev = nullptr;
   if (c->prof_on) {
@@ -319,6 +333,9 @@ rad_status enqueue_accumulate(rad_ctx* c, long long n, const double* r, const do
     a.prof_clk = c->d_prof_clk;
   }
   s = cuda_check(c, launch_prepass(a, (int)((n + 255) / 256), c->stream));
+  if (s == RAD_OK && a.any_wide)
+    s = cuda_check(c, launch_wide(a, (int)((n + kSortBlock - 1) / kSortBlock), (int)((n + 255) / 256),
+                                  c->stream));
   if (s != RAD_OK) return s;
   if (ev) cudaEventRecord(ev[1], c->stream);
   const long long grid = std::min<long long>(a.n_items, resident_ctas(variant));
@@ -438,6 +455,7 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
   js.n_bins = c->n_bins;
   fill_tiles(js, c->tile.variant, c->tile.omega_tile);
   js.tau_fast = (float)(2097152.0 / std::max(om_hi_max, 1e-300));  // 2^21 turns
+  wide_geometry(nd.data(), n_dir, js.tau_fast, js.axis, &js.bucket_w);
 
   rad_status s = RAD_OK;
   auto chk = [&](cudaError_t e) {
@@ -450,7 +468,7 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
   chk(dmalloc(&c->d_dir_tab, dir_tab.size()));
   chk(dmalloc(&c->d_ref, 4));
   chk(dmalloc(&c->d_status, 1));
-  chk(dmalloc(&c->d_counter, 1));
+  chk(dmalloc(&c->d_counter, kCounterWords));
   chk(dmalloc(&c->d_js, 1));
   chk(dmalloc(&c->d_spec, (size_t)3 * c->n_bins));
   if (prec == RAD_PREC_MIXED) {
@@ -501,6 +519,8 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
   js.literal = literal ? 1 : 0;
   js.f2_tab = c->d_f2;
   js.state_p = c->d_state_p;
+  // the wide flag lives in the counter block, zeroed before every call
+  js.wide_flag = c->d_counter ? reinterpret_cast<int*>(c->d_counter + 2) : nullptr;
   if (literal) {
     c->tile.variant = kLiteralVariant;
     c->tile.omega_tile = default_omega_tile(kLiteralVariant, n_omega);
@@ -521,7 +541,8 @@ void rad_destroy(rad_ctx* c) {
   void* ptrs[] = {c->d_omega, c->d_om_turns, c->d_om_tab, c->d_dirs, c->d_dir_tab, c->d_ref,
                   c->d_status, c->d_counter, c->d_js, c->d_spec, c->d_state, c->d_state64,
                   c->d_tile_cnt, c->h_js.rec, c->h_js.partials, c->d_stage, c->d_state_p,
-                  c->d_f2, c->h_js.partials_p, c->d_push, c->d_push_bdot};
+                  c->d_f2, c->h_js.partials_p, c->d_push, c->d_push_bdot, c->h_js.perm,
+                  c->h_js.sort_counts, c->h_js.bucket_base, c->h_js.gref};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);

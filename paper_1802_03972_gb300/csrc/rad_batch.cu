@@ -73,7 +73,10 @@ rad_status BatchCore::init(int max_jobs, cudaStream_t s) {
       cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming) != cudaSuccess)
     return RAD_ECUDA;
   if (cudaMalloc(&d_js, sizeof(JobStatic) * cap) != cudaSuccess) return RAD_ENOMEM;
-  if (cudaMalloc(&d_counter, sizeof(unsigned long long)) != cudaSuccess) return RAD_ENOMEM;
+  // Counter block: the two kernels' item counters, the launch's wide flag, then
+  // one wide flag (int) per job slot; zeroed before every round.
+  counter_bytes = kCounterWords * sizeof(unsigned long long) + sizeof(int) * (size_t)cap;
+  if (cudaMalloc(&d_counter, counter_bytes) != cudaSuccess) return RAD_ENOMEM;
   for (int k = 0; k < kSlots; ++k) {
     if (cudaMallocHost(&h_calls[k], sizeof(JobCall) * cap) != cudaSuccess) return RAD_ENOMEM;
     if (cudaMalloc(&d_calls[k], sizeof(JobCall) * cap) != cudaSuccess) return RAD_ENOMEM;
@@ -127,6 +130,10 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
       js.n_cap = c->h_js.n_cap;
       js.partials = c->h_js.partials;
       js.chunk_cap = c->h_js.chunk_cap;
+      js.perm = c->h_js.perm;
+      js.sort_counts = c->h_js.sort_counts;
+      js.bucket_base = c->h_js.bucket_base;
+      js.gref = c->h_js.gref;
     }
     plan.push_back({i, steps[i].n, ck, nch, (long long)js.n_tiles * nch * (long long)ck, js});
   }
@@ -134,6 +141,10 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
   // Largest jobs first, so the dynamic scheduler's tail holds small items.
   std::stable_sort(plan.begin(), plan.end(),
                    [](const Plan& a, const Plan& b) { return a.cost > b.cost; });
+  // Each job's wide flag is its slot in the batch's counter block.
+  int* wide_flags = reinterpret_cast<int*>(d_counter + kCounterWords);
+  for (size_t p = 0; p < plan.size(); ++p)
+    plan[p].js.wide_flag = plan[p].js.wide_flag ? wide_flags + p : nullptr;
 
   // Static job table (re-uploaded when the set or any context changed).
   bool js_changed = plan.size() != cur_jobs.size() || variant != cur_variant;
@@ -162,7 +173,7 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
   slot = (slot + 1) % kSlots;
   if (cudaEventSynchronize(slot_done[s]) != cudaSuccess) return RAD_ECUDA;
   long long items = 0;
-  int blocks = 0;
+  int blocks = 0, sort_blocks = 0;
   std::vector<rad_step> sorted(plan.size());
   for (size_t p = 0; p < plan.size(); ++p) {
     const rad_step& st = steps[plan[p].job];
@@ -180,8 +191,10 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
     K.n_chunks = plan[p].n_chunks;
     K.item_begin = items;
     K.block_begin = blocks;
+    K.sort_block_begin = sort_blocks;
     items += (long long)plan[p].js.n_tiles * plan[p].n_chunks;
     blocks += (int)((st.n + 255) / 256);
+    sort_blocks += (int)((st.n + kSortBlock - 1) / kSortBlock);
   }
   LaunchArgs a;
   memset(&a, 0, sizeof(a));
@@ -191,16 +204,20 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
   a.use_inline = 0;
   a.n_items = items;
   a.item_counter = d_counter;
+  a.any_wide = reinterpret_cast<int*>(d_counter + 2);
   const int grid = (int)std::min<long long>(items, resident_ctas(variant));
   const size_t call_bytes = sizeof(JobCall) * plan.size();
 
   auto enqueue = [&](cudaStream_t st) -> cudaError_t {
     cudaError_t e = cudaMemcpyAsync(d_calls[s], h_calls[s], call_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, counter_bytes, st);
     if (e == cudaSuccess) e = launch_prepass(a, blocks, st);
+    if (e == cudaSuccess) e = launch_wide(a, sort_blocks, blocks, st);
     if (e == cudaSuccess) e = launch_accumulate(variant, a, grid, st);
     return e;
   };
+  // kernels per round: pre-pass, the wide-call kernels, both accumulate kernels
+  const int launches = 1 + kWideLaunches + 2;
 
   // Order after the caller's stream (its inputs), run on the internal stream.
   cudaError_t e = cudaEventRecord(ev_in, stream);
@@ -208,7 +225,7 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
   if (e != cudaSuccess) return RAD_ECUDA;
   if (use_graphs && graph_exec[s] && same_signature(sig[s], sorted.data(), sorted.size())) {
     e = cudaGraphLaunch(graph_exec[s], work);
-    count_launches(2);
+    count_launches(launches);
   } else if (use_graphs) {
     if (graph_exec[s]) cudaGraphExecDestroy(graph_exec[s]);
     if (graph[s]) cudaGraphDestroy(graph[s]);
@@ -217,7 +234,7 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
     e = cudaStreamBeginCapture(work, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       cudaError_t e2 = enqueue(work);
-      count_launches(-2);  // captured, not launched
+      count_launches(-launches);  // captured, not launched
       e = cudaStreamEndCapture(work, &graph[s]);
       if (e2 != cudaSuccess) e = e2;
     }
@@ -225,7 +242,7 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
     if (e == cudaSuccess) {
       sig[s] = sorted;
       e = cudaGraphLaunch(graph_exec[s], work);
-      count_launches(2);
+      count_launches(launches);
     }
   } else {
     e = enqueue(work);

@@ -20,7 +20,8 @@ struct BatchCore {
   bool stream_ok = false;
   int cap = 0;
   JobStatic* d_js = nullptr;
-  unsigned long long* d_counter = nullptr;
+  unsigned long long* d_counter = nullptr;  // counter block (see init)
+  size_t counter_bytes = 0;
   JobCall* h_calls[kSlots] = {nullptr, nullptr};
   JobCall* d_calls[kSlots] = {nullptr, nullptr};
   cudaEvent_t slot_done[kSlots] = {nullptr, nullptr};

@@ -40,6 +40,22 @@ constexpr int kItemsPerCta = 24;
 constexpr int kMinChunk = 2048;
 static_assert(kMinChunk % kChunkAlign == 0, "the minimum chunk is a whole number of tiles");
 
+// Wide calls (particles farther than half the fast phase range from the
+// call's reference point): a stable bucket sort along the grid's mean
+// direction (kSortBuckets buckets of width bucket_w centred on the reference,
+// kSortBlock particles per histogram block) puts nearby particles next to
+// each other, and records are written relative to the first particle of
+// each sorted kGroup-particle group; the accumulate kernel rotates each tile's
+// sums by the group's reference phase.
+constexpr int kSortBlock = 2048;
+// A context's counter block (unsigned long long words, zeroed before every
+// call): [0], [1] the two accumulate kernels' work-item counters, [2] the
+// call's wide flag (an int).
+constexpr int kCounterWords = 3;
+constexpr int kSortBuckets = 4096;
+constexpr int kGroup = 256;
+static_assert(kGroup == kChunkAlign, "a work item holds whole sorted groups");
+
 // Device status bits (per job).
 // ST_BOUNDS: an index check of a debug build (RAD_DEBUG_BOUNDS) failed.
 // ST_BAD_GRID: a frequency or direction given in device memory (the
@@ -72,6 +88,15 @@ struct JobStatic {
   const float* f2_tab;            // [n_omega] f(omega)^2 of the creation shape
   float* state_p;                 // [8][n_bins]: P.e1, P.e2 re/im sums, then compensations
   float* partials_p;              // [chunk_cap][4][n_bins]
+  // wide calls (null wide_flag: never; the tiles of a spread call then take
+  // the FP64 phase path)
+  int* wide_flag;                 // per call: 1 if the call is wide (set by the pre-pass)
+  double axis[3];                 // sort axis: the grid's mean direction (unit)
+  double bucket_w;                // bucket width along the axis, m
+  int* perm;                      // [n_cap] sorted position -> particle index
+  int* sort_counts;               // [ceil(n_cap / kSortBlock)][kSortBuckets]
+  int* bucket_base;               // [kSortBuckets] first sorted position of each bucket
+  double* gref;                   // [ceil(n_cap / kGroup)][3] group reference - call reference, m
 };
 
 // Per-call data of one job.
@@ -86,7 +111,7 @@ struct JobCall {
   int n_chunks;
   long long item_begin;  // first global work item of this job
   int block_begin;       // first pre-pass block of this job
-  int pad_;
+  int sort_block_begin;  // first sort-histogram block of this job
 };
 
 struct LaunchArgs {
@@ -95,11 +120,16 @@ struct LaunchArgs {
   int n_jobs;
   int use_inline;        // 1: single job, call passed by value below
   long long n_items;
+  // [2] work-item counters: [0] the kernel for ordinary calls, [1] the kernel
+  // for wide calls (both zeroed before the launch)
   unsigned long long* item_counter;
   JobCall inline_call;
   // Profiling only (else null): [0] SM clock cycles and [1] nanoseconds, each
   // summed over the accumulate CTAs' lifetimes.
   unsigned long long* prof_clk;
+  // Set (non-zero) by the pre-pass when some job's call is wide; null when no
+  // job can be (the wide kernels are then not launched).
+  int* any_wide;
 };
 
 // Kernel variants of the mixed-precision accumulate kernel.
@@ -133,6 +163,17 @@ cudaError_t launch_readout_literal(const float* state_p, int n_bins, double* out
 
 // Launchers (rad_kernels.cu). All enqueue on `s` and return the launch error.
 cudaError_t launch_prepass(const LaunchArgs& a, int total_blocks, cudaStream_t s);
+// The wide-call kernels (histogram, scan, scatter, sorted records), launched
+// after the pre-pass; each returns at once for jobs whose call is not wide.
+// sort_blocks / prepass_blocks: the calls' ceil(n / kSortBlock) and
+// ceil(n / 256) summed over the jobs.  Adds 4 to the launch count.
+cudaError_t launch_wide(const LaunchArgs& a, int sort_blocks, int prepass_blocks, cudaStream_t s);
+constexpr int kWideLaunches = 4;
+// Sort axis and bucket width of a job (host, at creation).
+void wide_geometry(const double* unit_dirs, int n_dir, float tau_fast, double axis[3],
+                   double* bucket_w);
+// Launches the accumulate kernel for ordinary calls and, when a.any_wide is
+// set, the one for wide calls after it (one or two launches).
 cudaError_t launch_accumulate(int variant, const LaunchArgs& a, int grid, cudaStream_t s);
 int accumulate_blocks_per_sm(int variant);
 // Per-device caches of launch properties cover device ordinals below this.

@@ -32,6 +32,50 @@ constexpr double kPi = 3.14159265358979323846;
 // ------------------------------------------------------------------ prepass
 // Record layout (floats): 0-2 (r - r_ref)/c hi, 3-5 lo, 6-8 beta hi, 9-11 beta
 // lo, 12-14 beta_dot, 15 1/gamma^2, 16 w dt, 17 sqrt(w) dt, 18 w - 1, 19 unused.
+// Record of particle k with positions relative to rr; false for invalid data
+// (the record then has zero weights and a harmless finite beta).
+__device__ __forceinline__ bool make_record(const JobStatic& J, const JobCall& K, long long k,
+                                            const double rr[3], float v[kRecFields]) {
+  const long long n = K.n;
+  const double x = K.r[k], y = K.r[n + k], z = K.r[2 * n + k];
+  const double bx = K.beta[k], by = K.beta[n + k], bz = K.beta[2 * n + k];
+  const double ax = K.bdot[k], ay = K.bdot[n + k], az = K.bdot[2 * n + k];
+  const double w = K.w[k];
+  const double g2 = 1.0 - (bx * bx + by * by + bz * bz);
+  const bool valid = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(bx) && isfinite(by) &&
+                     isfinite(bz) && isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(w) &&
+                     w > 0.0 && g2 > 0.0 && isfinite(K.dt) && isfinite(K.t);
+  if (valid && !J.skip) {
+    dev::split_ff((x - rr[0]) * kInvC, v[0], v[3]);
+    dev::split_ff((y - rr[1]) * kInvC, v[1], v[4]);
+    dev::split_ff((z - rr[2]) * kInvC, v[2], v[5]);
+    dev::split_ff(bx, v[6], v[9]);
+    dev::split_ff(by, v[7], v[10]);
+    dev::split_ff(bz, v[8], v[11]);
+    v[12] = __double2float_rn(ax);
+    v[13] = __double2float_rn(ay);
+    v[14] = __double2float_rn(az);
+    v[15] = __double2float_rn(g2);
+    v[16] = __double2float_rn(w * K.dt);
+    v[17] = __double2float_rn(sqrt(w) * K.dt);
+    v[18] = __double2float_rn(w - 1.0);
+  } else {
+#pragma unroll
+    for (int f = 0; f < 19; ++f) v[f] = 0.0f;
+    v[8] = 0.5f;   // a harmless finite beta (zero weights)
+    v[15] = 0.75f;
+  }
+  v[19] = 0.0f;
+  return valid;
+}
+
+__device__ __forceinline__ void store_record(float* dst_rec, const float v[kRecFields]) {
+  float4* dst = reinterpret_cast<float4*>(dst_rec);
+#pragma unroll
+  for (int q = 0; q < kRecFields / 4; ++q)
+    dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
 __global__ void __launch_bounds__(256) prepass_kernel(LaunchArgs a) {
   const int j = dev::find_job_block(a, blockIdx.x);
   const JobStatic& J = a.js[j];
@@ -48,43 +92,209 @@ __global__ void __launch_bounds__(256) prepass_kernel(LaunchArgs a) {
     J.ref[3] = K.t;
   }
   if (k >= n) return;
-  const double x = K.r[k], y = K.r[n + k], z = K.r[2 * n + k];
-  const double bx = K.beta[k], by = K.beta[n + k], bz = K.beta[2 * n + k];
-  const double ax = K.bdot[k], ay = K.bdot[n + k], az = K.bdot[2 * n + k];
-  const double w = K.w[k];
-  const double g2 = 1.0 - (bx * bx + by * by + bz * bz);
-  const bool valid = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(bx) && isfinite(by) &&
-                     isfinite(bz) && isfinite(ax) && isfinite(ay) && isfinite(az) && isfinite(w) &&
-                     w > 0.0 && g2 > 0.0 && isfinite(K.dt) && isfinite(K.t);
-  const bool ok = valid && !J.skip;
   float v[kRecFields];
-  if (ok) {
-    dev::split_ff((x - rr[0]) * kInvC, v[0], v[3]);
-    dev::split_ff((y - rr[1]) * kInvC, v[1], v[4]);
-    dev::split_ff((z - rr[2]) * kInvC, v[2], v[5]);
-    dev::split_ff(bx, v[6], v[9]);
-    dev::split_ff(by, v[7], v[10]);
-    dev::split_ff(bz, v[8], v[11]);
-    v[12] = __double2float_rn(ax);
-    v[13] = __double2float_rn(ay);
-    v[14] = __double2float_rn(az);
-    v[15] = __double2float_rn(g2);
-    v[16] = __double2float_rn(w * K.dt);
-    v[17] = __double2float_rn(sqrt(w) * K.dt);
-    v[18] = __double2float_rn(w - 1.0);
-  } else {
-    if (!valid) atomicOr(J.status, ST_BAD_PARTICLE);
-#pragma unroll
-    for (int f = 0; f < 19; ++f) v[f] = 0.0f;
-    v[8] = 0.5f;   // a harmless finite beta (zero weights)
-    v[15] = 0.75f;
+  const bool valid = make_record(J, K, k, rr, v);
+  if (!valid) atomicOr(J.status, ST_BAD_PARTICLE);
+  // A particle farther than half the fast phase range from the reference makes
+  // the call wide (one atomic per warp that has one).
+  bool far = false;
+  if (J.wide_flag && valid && !J.skip && n < (1LL << 31)) {
+    const double dx = K.r[k] - rr[0], dy = K.r[n + k] - rr[1], dz = K.r[2 * n + k] - rr[2];
+    const double half = 0.5 * (double)J.tau_fast * kC;
+    far = dx * dx + dy * dy + dz * dz > half * half;
   }
-  v[19] = 0.0f;
+  const unsigned far_lanes = __ballot_sync(__activemask(), far);
+  if (far && (threadIdx.x & 31) == __ffs(far_lanes) - 1) {
+    atomicOr(J.wide_flag, 1);
+    if (a.any_wide && a.any_wide != J.wide_flag) atomicOr(a.any_wide, 1);
+  }
   if (!dev::bounds_ok(k < J.n_cap, J.status)) return;
-  float4* dst = reinterpret_cast<float4*>(J.rec + (size_t)k * kRecFields);
+  store_record(J.rec + (size_t)k * kRecFields, v);
+}
+
+// ------------------------------------------------------------- wide calls
+__device__ __forceinline__ bool call_is_wide(const JobStatic& J) {
+  return J.wide_flag != nullptr && *J.wide_flag != 0;
+}
+
+// Bucket of particle k along the sort axis, centred on the call's reference.
+// Explicit roundings: the histogram and the scatter kernels must agree bit for
+// bit, whatever either compilation contracts into fused multiply-adds.
+__device__ __forceinline__ int sort_bucket(const JobStatic& J, const JobCall& K, long long k) {
+  const long long n = K.n;
+  const double dx = __dsub_rn(K.r[k], J.ref[0]);
+  const double dy = __dsub_rn(K.r[n + k], J.ref[1]);
+  const double dz = __dsub_rn(K.r[2 * n + k], J.ref[2]);
+  const double s = __fma_rn(J.axis[0], dx, __fma_rn(J.axis[1], dy, __dmul_rn(J.axis[2], dz)));
+  const double q = __ddiv_rn(s, J.bucket_w);
+  constexpr double kHalf = 0.5 * kSortBuckets;
+  if (!(q > -kHalf)) return 0;  // also NaN
+  if (!(q < kHalf)) return kSortBuckets - 1;
+  return min(kSortBuckets - 1, (int)floor(q + kHalf));
+}
+
+// Job of a sort-histogram block (jobs ordered by sort_block_begin).
+__device__ __forceinline__ int find_job_sort_block(const LaunchArgs& a, int block) {
+  if (a.n_jobs == 1) return 0;
+  int lo = 0, hi = a.n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.jc[mid].sort_block_begin <= block) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Per kSortBlock particles: bucket counts.
+__global__ void __launch_bounds__(256) wide_hist_kernel(LaunchArgs a) {
+  const int j = find_job_sort_block(a, blockIdx.x);
+  const JobStatic& J = a.js[j];
+  if (!call_is_wide(J)) return;
+  const JobCall K = a.use_inline ? a.inline_call : a.jc[j];
+  __shared__ int hist[kSortBuckets];
+  for (int b = threadIdx.x; b < kSortBuckets; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  const long long blk = blockIdx.x - K.sort_block_begin;
+  const long long k0 = blk * kSortBlock;
+  for (int i = threadIdx.x; i < kSortBlock; i += blockDim.x)
+    if (k0 + i < K.n) atomicAdd(&hist[sort_bucket(J, K, k0 + i)], 1);
+  __syncthreads();
+  int* out = J.sort_counts + (size_t)blk * kSortBuckets;
+  for (int b = threadIdx.x; b < kSortBuckets; b += blockDim.x) out[b] = hist[b];
+}
+
+// One block per job: per bucket, the prefix of the counts over the histogram
+// blocks (in place), and the first sorted position of every bucket.
+__global__ void __launch_bounds__(1024) wide_scan_kernel(LaunchArgs a) {
+  const JobStatic& J = a.js[blockIdx.x];
+  if (!call_is_wide(J)) return;
+  const JobCall K = a.use_inline ? a.inline_call : a.jc[blockIdx.x];
+  __shared__ int tot[kSortBuckets];
+  __shared__ int wsum[32];
+  const int nblk = (int)((K.n + kSortBlock - 1) / kSortBlock);
+  for (int b = threadIdx.x; b < kSortBuckets; b += 1024) {
+    int run = 0;
+    int* c = J.sort_counts + b;
+    int blk = 0;
+    // eight independent loads in flight per step, then their prefix
+    for (; blk + 8 <= nblk; blk += 8) {
+      int v[8];
 #pragma unroll
-  for (int q = 0; q < kRecFields / 4; ++q)
-    dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      for (int u = 0; u < 8; ++u) v[u] = c[(size_t)(blk + u) * kSortBuckets];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        c[(size_t)(blk + u) * kSortBuckets] = run;
+        run += v[u];
+      }
+    }
+    for (; blk < nblk; ++blk) {
+      const int v = c[(size_t)blk * kSortBuckets];
+      c[(size_t)blk * kSortBuckets] = run;
+      run += v;
+    }
+    tot[b] = run;
+  }
+  __syncthreads();
+  static_assert(kSortBuckets == 4 * 1024, "four buckets per thread");
+  const int t = threadIdx.x, lane = t & 31;
+  const int v0 = tot[4 * t], v1 = tot[4 * t + 1], v2 = tot[4 * t + 2], v3 = tot[4 * t + 3];
+  const int s = v0 + v1 + v2 + v3;
+  int x = s;
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) wsum[t >> 5] = x;
+  __syncthreads();
+  if (t < 32) {
+    int w = wsum[t];
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, off);
+      if (t >= off) w += y;
+    }
+    wsum[t] = w;
+  }
+  __syncthreads();
+  const int excl = x - s + ((t >> 5) ? wsum[(t >> 5) - 1] : 0);
+  J.bucket_base[4 * t] = excl;
+  J.bucket_base[4 * t + 1] = excl + v0;
+  J.bucket_base[4 * t + 2] = excl + v0 + v1;
+  J.bucket_base[4 * t + 3] = excl + v0 + v1 + v2;
+}
+
+// Per kSortBlock particles: the sorted position of every particle, stable
+// (particles of one bucket keep their order), so the order is a function of
+// the input alone.  The block computes the buckets into shared memory, then
+// one warp hands out the positions in particle order.
+__global__ void __launch_bounds__(256) wide_scatter_kernel(LaunchArgs a) {
+  const int j = find_job_sort_block(a, blockIdx.x);
+  const JobStatic& J = a.js[j];
+  if (!call_is_wide(J)) return;
+  const JobCall K = a.use_inline ? a.inline_call : a.jc[j];
+  __shared__ int cnt[kSortBuckets];
+  __shared__ int bkt[kSortBlock];
+  const long long blk = blockIdx.x - K.sort_block_begin;
+  const long long k0 = blk * kSortBlock;
+  const int* pre = J.sort_counts + (size_t)blk * kSortBuckets;
+  for (int b = threadIdx.x; b < kSortBuckets; b += blockDim.x) cnt[b] = J.bucket_base[b] + pre[b];
+  for (int i = threadIdx.x; i < kSortBlock; i += blockDim.x)
+    bkt[i] = k0 + i < K.n ? sort_bucket(J, K, k0 + i) : -1;
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const unsigned below = (1u << lane) - 1u;
+  for (int it = 0; it < kSortBlock / 32; ++it) {
+    const long long k = k0 + it * 32 + lane;
+    const bool in = k < K.n;
+    const int b = bkt[it * 32 + lane];
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int pos = in ? cnt[b] + __popc(peers & below) : 0;
+    __syncwarp();
+    if (in) {
+      // positions are in [0, n) by construction; an inconsistency is reported
+      // (the context then fails) instead of written
+      if (pos >= 0 && pos < K.n) J.perm[pos] = (int)k;
+      else atomicOr(J.status, ST_BOUNDS);
+      if (lane == 31 - __clz(peers)) cnt[b] += __popc(peers);
+    }
+    __syncwarp();
+  }
+}
+
+// Records in sorted order, positions relative to the first particle of each
+// kGroup-particle group (its reference point); the group references relative
+// to the call's reference go to gref.
+__global__ void __launch_bounds__(256) wide_records_kernel(LaunchArgs a) {
+  const int j = dev::find_job_block(a, blockIdx.x);
+  const JobStatic& J = a.js[j];
+  if (!call_is_wide(J)) return;
+  const JobCall K = a.use_inline ? a.inline_call : a.jc[j];
+  static_assert(kGroup == 256, "one block per group");
+  const long long p0 = (long long)(blockIdx.x - K.block_begin) * kGroup;
+  const long long p = p0 + threadIdx.x;
+  if (p >= K.n) return;
+  const long long n = K.n;
+  int k = J.perm[p], k0 = J.perm[p0];
+  if (k < 0 || k >= n || k0 < 0 || k0 >= n) {  // never, for a consistent sort
+    atomicOr(J.status, ST_BOUNDS);
+    k = k0 = 0;
+  }
+  double R[3] = {K.r[k0], K.r[n + k0], K.r[2 * n + k0]};
+  if (!(isfinite(R[0]) && isfinite(R[1]) && isfinite(R[2]))) {
+    R[0] = J.ref[0];
+    R[1] = J.ref[1];
+    R[2] = J.ref[2];
+  }
+  float v[kRecFields];
+  make_record(J, K, k, R, v);  // invalid data was reported by the pre-pass
+  if (!dev::bounds_ok(p < J.n_cap, J.status)) return;
+  store_record(J.rec + (size_t)p * kRecFields, v);
+  if (threadIdx.x == 0) {
+    double* g = J.gref + 3 * (p0 / kGroup);
+    g[0] = R[0] - J.ref[0];
+    g[1] = R[1] - J.ref[1];
+    g[2] = R[2] - J.ref[2];
+  }
 }
 
 // ------------------------------------------------------------------ readout
@@ -283,6 +493,32 @@ cudaError_t launch_prepass(const LaunchArgs& a, int total_blocks, cudaStream_t s
   prepass_kernel<<<total_blocks, 256, 0, s>>>(a);
   count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_wide(const LaunchArgs& a, int sort_blocks, int prepass_blocks, cudaStream_t s) {
+  if (sort_blocks <= 0 || prepass_blocks <= 0) return cudaSuccess;
+  wide_hist_kernel<<<sort_blocks, 256, 0, s>>>(a);
+  wide_scan_kernel<<<a.n_jobs, 1024, 0, s>>>(a);
+  wide_scatter_kernel<<<sort_blocks, 256, 0, s>>>(a);
+  wide_records_kernel<<<prepass_blocks, 256, 0, s>>>(a);
+  count_launches(kWideLaunches);
+  return cudaGetLastError();
+}
+
+void wide_geometry(const double* nd, int n_dir, float tau_fast, double axis[3], double* bucket_w) {
+  double m[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < n_dir; ++d)
+    for (int i = 0; i < 3; ++i) m[i] += nd[3 * d + i];
+  double len = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+  // A grid spread over all directions has no useful mean: sort along z.
+  if (!(len > 0.5 * n_dir)) {
+    m[0] = m[1] = 0.0;
+    m[2] = len = 1.0;
+  }
+  for (int i = 0; i < 3; ++i) axis[i] = m[i] / len;
+  // A group of sorted particles spans about two buckets along the axis: an
+  // eighth of the fast range keeps it well inside.
+  *bucket_w = (double)tau_fast * kC / 8.0;
 }
 
 cudaError_t launch_readout(const float* state, int mixed, const double* state64, int n_omega,

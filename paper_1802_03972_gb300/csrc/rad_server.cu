@@ -83,8 +83,10 @@ size_t estimate_footprint(const rad_job_desc& d) {
   const size_t by_particles = nb * (size_t)((d.max_particles + kChunkAlign - 1) / kChunkAlign);
   const size_t by_items = (size_t)kItemsPerCta * resident_ctas(kDefaultVariant) * bins_per_tile + nb;
   const size_t partials = 32 * std::min(by_particles, by_items);
-  return nb * (64 + 24) + partials + (size_t)d.max_particles * 80 * (1 + d.max_queued) +
-         (size_t)d.n_omega * 48 + (size_t)d.n_dir * 72 + (1 << 16);
+  // Records (80 B per particle), the sort buffers of wide calls (13 B) and the
+  // queued steps' staging slots (80 B each).
+  return nb * (64 + 24) + partials + (size_t)d.max_particles * (80 + 13 + 80 * (size_t)d.max_queued) +
+         (size_t)d.n_omega * 48 + (size_t)d.n_dir * 72 + (1 << 16) + 4 * (size_t)kSortBuckets;
 }
 
 }  // namespace

@@ -93,11 +93,22 @@ __device__ __forceinline__ float2 phase2(float2 omh, float2 wh, float2 wl, float
   return __ffma2_rn(f0, k2Pi, c2);
 }
 
-// Phase in FP64 (wide path): omega/2pi times the float-float dtau, reduced.
-__device__ __forceinline__ float phase_wide(double om_turns, float th, float tl) {
-  double x = om_turns * ((double)th + (double)tl);
+// Phase in FP64 (wide path): omega/2pi times the float-float dtau plus an
+// offset (the tile group's reference time in a wide call), reduced.
+__device__ __forceinline__ float phase_wide(double om_turns, float th, float tl, double off = 0.0) {
+  double x = om_turns * ((double)th + (double)tl + off);
   x -= rint(x);
   return (float)(x * 6.283185307179586);
+}
+
+// e^{i 2 pi omega_turns tau} in FP32 (tau: a group's reference time in a wide
+// call, up to ~1e-11 s), the phase reduced in FP64.
+__device__ __forceinline__ void group_rotation(double om_turns, double tau, float& c, float& s) {
+  double x = om_turns * tau;
+  x -= rint(x);
+  const float ph = (float)(x * 6.283185307179586);
+  c = cos_approx(ph);
+  s = sin_approx(ph);
 }
 
 }  // namespace dev
