@@ -80,7 +80,8 @@ def parse():
                    help="skip the literal-sum, in-situ coupling and 3-D readout timings")
     p.add_argument("--serve-policy", default=None,
                    help="round policy 'P,ROUND_UPDATES' of the serving legs (0 all, 1 oldest, "
-                        "2 least served, 3 least served with aging; default: the library's)")
+                        "2 least served, 3 least served with aging, 4 oldest with bounded "
+                        "backfill; default: the library's)")
     p.add_argument("--serve-rate", type=float, default=None,
                    help="fixed arrival rate (jobs/s) instead of --serve-load")
     p.add_argument("--peaks", action="store_true", help="also run the pipe-throughput probe")

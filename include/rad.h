@@ -307,17 +307,17 @@ rad_status rad_server_create(size_t hbm_budget, int32_t max_slots, void* stream,
  *   RAD_SERVE_ALL: every admitted job with a step ready (equal shares);
  *   RAD_SERVE_OLDEST: jobs in arrival order until the round holds round_updates
  *     amplitude updates (particles x bins), at least one job;
- *   RAD_SERVE_LEAST_SERVED (default, round_updates = 2e10): the same in order of
+ *   RAD_SERVE_LEAST_SERVED: the same in order of
  *     the updates each job has had so far (new and small jobs first; ties in
  *     arrival order);
  *   RAD_SERVE_LEAST_SERVED_AGED: as least served, with each job's updates reduced
  *     by its time since submission times one round's updates per 12 ms, so that
  *     large jobs that have waited long are not passed over indefinitely;
- *   RAD_SERVE_OLDEST_BACKFILL: the oldest job with a step ready always; the
- *     others, least served first, each only if the round's updates stay within
- *     max(round_updates, 17/16 of the oldest job's step), so the oldest job runs
- *     at >= 16/17 of its own pace (the tail latency of a FIFO queue) while small
- *     jobs progress in the margin.
+ *   RAD_SERVE_OLDEST_BACKFILL (default, round_updates = 2e9): the oldest job
+ *     with a step ready always; the others, least served first, each only if
+ *     the round's updates stay within max(round_updates, 17/16 of the oldest
+ *     job's step), so the oldest job runs at >= 16/17 of its own pace (the tail
+ *     latency of a FIFO queue) while small jobs progress in the margin.
  * round_updates >= 1 for all but RAD_SERVE_ALL, which ignores it.  Takes effect
  * from the next round.  RAD_EINVAL for an unknown policy or round_updates < 1. */
 enum { RAD_SERVE_ALL = 0, RAD_SERVE_OLDEST = 1, RAD_SERVE_LEAST_SERVED = 2, RAD_SERVE_LEAST_SERVED_AGED = 3,
