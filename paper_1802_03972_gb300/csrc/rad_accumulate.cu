@@ -702,7 +702,11 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
 // the common path keeps its register allocation free of the wide-call code.
 template <int THREADS, int W, int MINB, bool TC, bool LIT, int PASSES = 1, bool WIDE = false>
 __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a) {
-  if (WIDE && (a.any_wide == nullptr || *a.any_wide == 0)) return;
+  // Whether any job of the launch is wide is final before either kernel starts:
+  // the wide one leaves at once without, and the ordinary one then takes every
+  // item without looking at the jobs' flags.
+  const bool any_wide = a.any_wide != nullptr && *a.any_wide != 0;
+  if (WIDE && !any_wide) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ long long s_item[2];
@@ -730,7 +734,7 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     if (item >= a.n_items) break;
     const int j = find_job(a, item);
     const JobStatic& J = a.js[j];
-    if ((J.wide_flag != nullptr && *J.wide_flag != 0) != WIDE) continue;  // the other kernel's
+    if (any_wide && (J.wide_flag != nullptr && *J.wide_flag != 0) != WIDE) continue;  // the other kernel's
     const JobCall K = a.use_inline ? a.inline_call : a.jc[j];
     const long long local = item - K.item_begin;
     // Tile-major order: the chunks of one tile run close together in time, so

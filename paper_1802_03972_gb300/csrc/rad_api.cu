@@ -455,7 +455,7 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
   js.n_bins = c->n_bins;
   fill_tiles(js, c->tile.variant, c->tile.omega_tile);
   js.tau_fast = (float)(2097152.0 / std::max(om_hi_max, 1e-300));  // 2^21 turns
-  wide_geometry(nd.data(), n_dir, js.tau_fast, js.axis, &js.bucket_w);
+  wide_geometry(nd.data(), n_dir, js.tau_fast, js.axis, &js.cone_sin, &js.bucket_w);
 
   rad_status s = RAD_OK;
   auto chk = [&](cudaError_t e) {

@@ -92,6 +92,7 @@ struct JobStatic {
   // the FP64 phase path)
   int* wide_flag;                 // per call: 1 if the call is wide (set by the pre-pass)
   double axis[3];                 // sort axis: the grid's mean direction (unit)
+  double cone_sin;                // sine of the largest angle of a direction from the axis (1 past 90 deg)
   double bucket_w;                // bucket width along the axis, m
   int* perm;                      // [n_cap] sorted position -> particle index
   int* sort_counts;               // [ceil(n_cap / kSortBlock)][kSortBuckets]
@@ -171,7 +172,7 @@ cudaError_t launch_wide(const LaunchArgs& a, int sort_blocks, int prepass_blocks
 constexpr int kWideLaunches = 4;
 // Sort axis and bucket width of a job (host, at creation).
 void wide_geometry(const double* unit_dirs, int n_dir, float tau_fast, double axis[3],
-                   double* bucket_w);
+                   double* cone_sin, double* bucket_w);
 // Launches the accumulate kernel for ordinary calls and, when a.any_wide is
 // set, the one for wide calls after it (one or two launches).
 cudaError_t launch_accumulate(int variant, const LaunchArgs& a, int grid, cudaStream_t s);

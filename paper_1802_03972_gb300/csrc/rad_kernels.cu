@@ -13,6 +13,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "rad_device.cuh"
@@ -95,13 +96,16 @@ __global__ void __launch_bounds__(256) prepass_kernel(LaunchArgs a) {
   float v[kRecFields];
   const bool valid = make_record(J, K, k, rr, v);
   if (!valid) atomicOr(J.status, ST_BAD_PARTICLE);
-  // A particle farther than half the fast phase range from the reference makes
-  // the call wide (one atomic per warp that has one).
+  // A particle that some direction of the grid may see beyond the fast phase
+  // range makes the call wide (one atomic per warp that has one).  The bound
+  // on |n . (r - r_ref)| over the grid: |axis . dr| + sin(largest angle from
+  // the axis) |dr across the axis|.
   bool far = false;
   if (J.wide_flag && valid && !J.skip && n < (1LL << 31)) {
     const double dx = K.r[k] - rr[0], dy = K.r[n + k] - rr[1], dz = K.r[2 * n + k] - rr[2];
-    const double half = 0.5 * (double)J.tau_fast * kC;
-    far = dx * dx + dy * dy + dz * dz > half * half;
+    const double along = J.axis[0] * dx + J.axis[1] * dy + J.axis[2] * dz;
+    const double across = sqrt(fmax(dx * dx + dy * dy + dz * dz - along * along, 0.0));
+    far = fabs(along) + J.cone_sin * across > 0.999 * (double)J.tau_fast * kC;
   }
   const unsigned far_lanes = __ballot_sync(__activemask(), far);
   if (far && (threadIdx.x & 31) == __ffs(far_lanes) - 1) {
@@ -505,7 +509,8 @@ cudaError_t launch_wide(const LaunchArgs& a, int sort_blocks, int prepass_blocks
   return cudaGetLastError();
 }
 
-void wide_geometry(const double* nd, int n_dir, float tau_fast, double axis[3], double* bucket_w) {
+void wide_geometry(const double* nd, int n_dir, float tau_fast, double axis[3], double* cone_sin,
+                   double* bucket_w) {
   double m[3] = {0.0, 0.0, 0.0};
   for (int d = 0; d < n_dir; ++d)
     for (int i = 0; i < 3; ++i) m[i] += nd[3 * d + i];
@@ -516,6 +521,10 @@ void wide_geometry(const double* nd, int n_dir, float tau_fast, double axis[3], 
     m[2] = len = 1.0;
   }
   for (int i = 0; i < 3; ++i) axis[i] = m[i] / len;
+  double cos_min = 1.0;
+  for (int d = 0; d < n_dir; ++d)
+    cos_min = std::min(cos_min, axis[0] * nd[3 * d] + axis[1] * nd[3 * d + 1] + axis[2] * nd[3 * d + 2]);
+  *cone_sin = cos_min <= 0.0 ? 1.0 : sqrt(std::max(0.0, 1.0 - cos_min * cos_min));
   // A group of sorted particles spans about two buckets along the axis: an
   // eighth of the fast range keeps it well inside.
   *bucket_w = (double)tau_fast * kC / 8.0;
