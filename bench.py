@@ -74,6 +74,8 @@ def parse():
                    help="skip the in-situ-scale leg (1e7 particles, 1024 x 32^2 bins)")
     p.add_argument("--no-horizon", action="store_true",
                    help="skip the 256-step accuracy leg")
+    p.add_argument("--no-helix", action="store_true",
+                   help="skip the tiny helix leg (1000 small steps, mixed, FP64 and oracle)")
     p.add_argument("--serve-load", type=float, default=0.7,
                    help="arrival rate as a fraction of measured capacity")
     p.add_argument("--no-modes", action="store_true",
@@ -630,8 +632,13 @@ def insitu_leg(n_total: int = 10_000_000, n_chunk: int = 1_000_000, fp64_sample:
     bins = [(int(rng.integers(0, 1024)), int(rng.integers(0, 1024))) for _ in range(32)]
     bo, bd = oracle.grid_bins(omega, dirs, bins)
     acc = oracle.Accumulator(bo, bd, oracle.FF_CIC, 0.1e-6)
+    t0 = time.perf_counter()
     for st in chunks:
         acc.accumulate(st.r, st.beta, st.beta_dot, st.w, st.t, st.dt)
+    el_oracle = time.perf_counter() - t0
+    out["oracle"] = {"value": len(bins) * n_total / el_oracle, "unit": UNIT,
+                     "cores": oracle.num_threads(),
+                     "sample": f"{len(bins)} sampled bins x all {n_total} particles of the step"}
     acc_out = {}
     for name, kind in (("cic", oracle.FF_CIC), ("tsc", oracle.FF_TSC)):
         ref = acc.spectra(kind, 0.1e-6)
@@ -649,6 +656,53 @@ def insitu_leg(n_total: int = 10_000_000, n_chunk: int = 1_000_000, fp64_sample:
         acc_out[name] = {"bin_excess": worst, "tot_bin_rel_max": max(tot_rel)}
     out["vs_oracle_32_sampled_bins"] = acc_out
     ctx.close()
+    return out
+
+
+def helix_leg():
+    """The tiny helix workload (64 point particles, 1000 steps of 1e-17 s, 128 x 16
+    bins): the mixed path and the plain FP64 kernel over all 1000 steps through
+    the C ABI (device arrays resident), the oracle on the full grid on the host
+    cores, and both GPU paths' errors against it."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1802_03972_gb300 import inputs, rad
+    wl = inputs.tiny_helix()
+    steps = [wl.step(s) for s in range(wl.n_steps)]
+    dev = [[torch.from_numpy(a).cuda() for a in (st.r, st.beta, st.beta_dot, st.w)] for st in steps]
+    upd = wl.updates_per_step() * wl.n_steps
+    out = {"workload": "64 point macro-particles on gamma = 50 helices, 1000 steps of 1e-17 s, "
+                       "128 linear omega 1e15-1e18 rad/s x 16 directions 0-20 mrad",
+           "updates": upd}
+    spectra = {}
+    for name, prec in (("mixed", rad.PREC_MIXED), ("fp64_plain", rad.PREC_FP64)):
+        ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width, prec=prec)
+        ctx.accumulate(*dev[0], steps[0].t, steps[0].dt)  # warm-up
+        ctx.reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for d, st in zip(dev, steps):
+            ctx.accumulate(*d, st.t, st.dt)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"value": upd / (e0.elapsed_time(e1) / 1e3), "unit": UNIT}
+        spectra[name] = dict(zip(("coh", "inc", "tot"), ctx.spectrum()))
+        ctx.close()
+    bo, bd = oracle.grid_bins(wl.omega, wl.dirs)
+    acc = oracle.Accumulator(bo, bd, wl.ff_kind, wl.ff_width)
+    t0 = time.perf_counter()
+    for st in steps:
+        acc.accumulate(st.r, st.beta, st.beta_dot, st.w, st.t, st.dt)
+    el = time.perf_counter() - t0
+    out["oracle"] = {"value": upd / el, "unit": UNIT, "cores": oracle.num_threads(),
+                     "sample": "the full grid, all steps"}
+    shape = (wl.dirs.shape[0], wl.omega.shape[0])
+    ref = {k: v.reshape(shape) for k, v in acc.spectra().items()}
+    for name in ("mixed", "fp64_plain"):
+        out[name]["vs_oracle"] = {k: error_stats(spectra[name][k], ref[k]) for k in ("tot", "coh")}
     return out
 
 
@@ -899,6 +953,9 @@ def main():
     insitu = None
     if rank == 0 and not args.no_insitu:
         insitu = insitu_leg()
+    helix = None
+    if rank == 0 and not args.no_helix:
+        helix = helix_leg()
 
     batched = batched_small = None
     if not args.no_batch and rank == 0:
@@ -945,7 +1002,8 @@ def main():
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clocks, "rel_err_sampled": rel_err, "accuracy": accuracy, "fp64_plain": fp64,
                "modes": modes, "batched": batched, "batched_small_jobs": batched_small,
-               "insitu_scale": insitu, "accuracy_horizon": horizon, "sharded": sharded,
+               "insitu_scale": insitu, "tiny_helix": helix, "accuracy_horizon": horizon,
+               "sharded": sharded,
                "serving": served,
                "serving_literal_rate": served_literal,
                "p50_s": served["p50_s"] if served else None,
