@@ -138,6 +138,14 @@ rad_status rad_create(const double* omega, int32_t n_omega, const double* dirs, 
  *  t, dt    time of the step and its length, s (dt > 0).
  * Host pointers are accepted too: they are copied to library staging buffers
  * inside the call (pinned memory makes the copy asynchronous).
+ * The phase is computed in FP32 about one reference point per call (the first
+ * particle), which covers particles within 2^21 turns of the highest frequency
+ * from it (40 um at 1e20 rad/s, seen from any direction of the grid).  A call
+ * spread wider (all macro-particles of a simulation domain, Sec. 3.3) is sorted
+ * on the device along the grid's mean direction and given one reference point
+ * per 256 particles; its results are as deterministic as any other call's.
+ * The context keeps ~92 bytes of device memory per macro-particle of the
+ * largest call (records and sort buffers).
  * Errors: RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ESTATE. */
 rad_status rad_accumulate(rad_ctx* ctx, int64_t n, const double* r, const double* beta,
                           const double* beta_dot, const double* w, double t, double dt);

@@ -153,3 +153,57 @@ def test_wide_job_in_a_batch_equals_alone():
     for k, g in zip(("coh", "inc", "tot"), ctxs[0].spectrum()):
         assert_parity(g, acc.spectra()[k].reshape(shape), what=k)
     batch.close()
+
+
+def test_compact_and_wide_calls_alternate_on_one_context():
+    """The wide flag belongs to the call: a context fed a compact call, a wide
+    one, a compact one and a wide one (different particle counts) matches the
+    oracle fed the same calls."""
+    omega, dirs, r, b, bd, w = wide_bunch(5000, 1e-3, seed=37)
+    compact = inputs.BetatronBunch(3000, seed=38)
+    bo, bdir = oracle.grid_bins(omega, dirs)
+    acc = oracle.Accumulator(bo, bdir, oracle.FF_GAUSS, 0.1e-6)
+    ctx = rad.Context(omega, dirs, rad.FF_GAUSS, 0.1e-6)
+    wide_data = list(steps(r, b, bd, w, n_steps=2))
+    for s in range(4):
+        if s % 2 == 0:
+            st = compact.step(s * 1e-16, 1e-16)
+            call = (st.r.reshape(3, -1), st.beta.reshape(3, -1), st.beta_dot.reshape(3, -1), st.w,
+                    st.t, st.dt)
+        else:
+            call = wide_data[s // 2]
+        acc.accumulate(*call)
+        ctx.accumulate(*(to_dev(np.ascontiguousarray(x)) for x in call[:4]), call[4], call[5])
+    shape = (dirs.shape[0], omega.shape[0])
+    for k, g in zip(("coh", "inc", "tot"), ctx.spectrum()):
+        assert_parity(g, acc.spectra()[k].reshape(shape), what=k)
+
+
+def test_wide_bunch_through_the_in_situ_coupling():
+    """rad_push_step with a wide bunch (beta_dot differenced on the device): the
+    same spectra as feeding the differenced beta_dot to rad_accumulate."""
+    omega, dirs, r, b, bd, w = wide_bunch(4000, 1e-3, seed=39)
+    dt = 1e-16
+    # beta rotating slowly so that the differences are not zero
+    rots = [np.array([np.cos(1e-3 * s), np.sin(1e-3 * s)]) for s in range(4)]
+    betas = []
+    for c, s_ in rots:
+        bb = b.copy()
+        bb[0], bb[1] = c * b[0] - s_ * b[1], s_ * b[0] + c * b[1]
+        betas.append(bb)
+    rs = [r + betas[s] * C * s * dt for s in range(4)]
+    push = rad.Context(omega, dirs, rad.FF_GAUSS, 0.1e-6)
+    for s in range(4):
+        push.push_step(to_dev(rs[s]), to_dev(betas[s]), to_dev(w), s * dt, dt)
+    push.push_flush()
+    ref = rad.Context(omega, dirs, rad.FF_GAUSS, 0.1e-6)
+    for s in range(4):
+        if s == 0:
+            bdot = (betas[1] - betas[0]) / dt
+        elif s == 3:
+            bdot = (betas[3] - betas[2]) / dt
+        else:
+            bdot = (betas[s + 1] - betas[s - 1]) / (2 * dt)
+        ref.accumulate(to_dev(rs[s]), to_dev(betas[s]), to_dev(bdot), to_dev(w), s * dt, dt)
+    for a_, b_ in zip(push.spectrum(), ref.spectrum()):
+        assert_parity(a_, b_, what="push vs accumulate")
