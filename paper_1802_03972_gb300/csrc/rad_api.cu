@@ -301,7 +301,9 @@ rad_status enqueue_accumulate(rad_ctx* c, long long n, const double* r, const do
   a.use_inline = 1;
   a.n_items = (long long)c->h_js.n_tiles * n_chunks;
   a.item_counter = c->d_counter;  // [0], [1]: item counters; [2]: the wide flag
-  a.any_wide = c->h_js.wide_flag;
+  // A call of at most one sorted group is never wide (the pre-pass does not
+  // flag it): it needs neither the wide-call kernels nor the second kernel.
+  a.any_wide = n > kGroup ? c->h_js.wide_flag : nullptr;
   JobCall& K = a.inline_call;
   K.n = n;
   K.r = r;

@@ -100,8 +100,9 @@ __global__ void __launch_bounds__(256) prepass_kernel(LaunchArgs a) {
   // range makes the call wide (one atomic per warp that has one).  The bound
   // on |n . (r - r_ref)| over the grid: |axis . dr| + sin(largest angle from
   // the axis) |dr across the axis|.
+  // A call of one sorted group or less gains nothing from sorting: never wide.
   bool far = false;
-  if (J.wide_flag && valid && !J.skip && n < (1LL << 31)) {
+  if (J.wide_flag && valid && !J.skip && n > kGroup && n < (1LL << 31)) {
     const double dx = K.r[k] - rr[0], dy = K.r[n + k] - rr[1], dz = K.r[2 * n + k] - rr[2];
     const double along = J.axis[0] * dx + J.axis[1] * dy + J.axis[2] * dz;
     const double across = sqrt(fmax(dx * dx + dy * dy + dz * dz - along * along, 0.0));
