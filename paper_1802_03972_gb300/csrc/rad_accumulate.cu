@@ -32,6 +32,12 @@
 //    hi.hi + hi.lo + lo.hi + lo.lo with FP32 accumulation.  This takes the
 //    accumulation FMAs off the FP32 pipe, which together with the phase
 //    arithmetic and MUFU issue is what limits the FP32 variants.
+// Wide calls (particles spread beyond the fast phase range about the call's
+// reference point, sorted by the wide-call kernels) run in a second
+// instantiation (WIDE): their records are relative to the first particle of
+// each 256-particle group, so stage 1 and the update loop are unchanged, and
+// each tile's sums are rotated by e^{i omega tau_group} before they join the
+// chunk sums.
 // Sums are two-level (per particle tile, then per chunk).  Each work item
 // writes its partial sums; the last item of a bin tile to finish (an arrival
 // counter, no float atomics) adds the partials in chunk order, multiplies by
@@ -389,19 +395,19 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
     // has tau_g in every phase).
     if constexpr (wide) {
       if (!(flags & 1)) {
-      const double tau_g = group_tau(J, kt, my_d);
+        const double tau_g = group_tau(J, kt, my_d);
 #pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        float2 cs, sn;
-        group_rotation(J.om_turns[min(om_first + 2 * p, n_om - 1)], tau_g, cs.x, sn.x);
-        group_rotation(J.om_turns[min(om_first + 2 * p + 1, n_om - 1)], tau_g, cs.y, sn.y);
+        for (int p = 0; p < NP; ++p) {
+          float2 cs, sn;
+          group_rotation(J.om_turns[min(om_first + 2 * p, n_om - 1)], tau_g, cs.x, sn.x);
+          group_rotation(J.om_turns[min(om_first + 2 * p + 1, n_om - 1)], tau_g, cs.y, sn.y);
 #pragma unroll
-        for (int c = 0; c < NC; c += 2) {
-          const float2 re = acc1[p][c], im = acc1[p][c + 1];
-          acc1[p][c] = __ffma2_rn(re, cs, __fmul2_rn(make_float2(-im.x, -im.y), sn));
-          acc1[p][c + 1] = __ffma2_rn(re, sn, __fmul2_rn(im, cs));
+          for (int c = 0; c < NC; c += 2) {
+            const float2 re = acc1[p][c], im = acc1[p][c + 1];
+            acc1[p][c] = __ffma2_rn(re, cs, __fmul2_rn(make_float2(-im.x, -im.y), sn));
+            acc1[p][c + 1] = __ffma2_rn(re, sn, __fmul2_rn(im, cs));
+          }
         }
-      }
       }
     }
     // Two-level summation: the tile's sums join the chunk sums.
