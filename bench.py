@@ -76,6 +76,9 @@ def parse():
                    help="skip the 256-step accuracy leg")
     p.add_argument("--no-helix", action="store_true",
                    help="skip the tiny helix leg (1000 small steps, mixed, FP64 and oracle)")
+    p.add_argument("--wide-only", action="store_true",
+                   help="profiling aid: run only the wide-bunch leg for --steps steps (after one "
+                        "warm-up call) and print its figures")
     p.add_argument("--serve-load", type=float, default=0.7,
                    help="arrival rate as a fraction of measured capacity")
     p.add_argument("--no-modes", action="store_true",
@@ -767,6 +770,10 @@ def main():
     ring_dev = [[torch.from_numpy(a).to(dev) for a in (st.r, st.beta, st.beta_dot, st.w)]
                 for st in steps_host]
     upd = wl.updates_per_step()
+    if args.wide_only:
+        tile = tuple(int(x) for x in args.tile.split(",")) if args.tile else (8, 512, 0)
+        print(json.dumps({"wide_bunch": wide_leg(wl, tile, n_steps=args.steps)}), flush=True)
+        return
     ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
     if args.tile:
         ctx.set_tile(*[int(x) for x in args.tile.split(",")])
