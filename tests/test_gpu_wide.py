@@ -224,3 +224,28 @@ def test_wide_bunch_over_fifty_steps():
         if s + 1 in (10, 50):
             for k, g in zip(("coh", "inc", "tot"), ctx.spectrum()):
                 assert_parity(g, acc.spectra()[k].reshape(shape), what=f"{k} after {s + 1} steps")
+
+
+@pytest.mark.parametrize("variant", [0, 8])
+def test_wide_call_tiles_on_the_fp64_path(variant):
+    """A bunch 1 mm wide across the sort axis as well as along it, observed over
+    +-0.3 rad: sorting along the mean direction cannot make the groups compact
+    for the oblique directions, so some tiles take the per-update FP64 phase
+    path with their group's reference time added, others the rotated FP32
+    path; all against the oracle."""
+    # 30000 particles: groups of 256 span ~8 um along z (fast for the directions
+    # with no x component), ~1 mm across it (FP64 path for the oblique ones);
+    # 512 frequencies make every tile one direction, so both paths occur
+    rng = np.random.default_rng(41)
+    n = 30000
+    r = np.stack([rng.uniform(-5e-4, 5e-4, n), rng.normal(0, 2e-6, n), rng.uniform(-5e-4, 5e-4, n)])
+    b = np.stack([rng.normal(0, 1e-3, n), rng.normal(0, 1e-3, n), np.zeros(n)])
+    b[2] = np.sqrt(1 - 1.1e-5 - b[0] ** 2 - b[1] ** 2)
+    bd = rng.normal(0, 1e13, (3, n))
+    w = rng.uniform(1e3, 1e5, n)
+    omega = inputs.omega_log(1e16, 1e20, 512)
+    dirs = inputs.dirs_grid(0.3, 3, 3)
+    ctx, acc, shape = run_pair(omega, dirs, list(steps(r, b, bd, w, n_steps=2)), tile=(variant, 0, 0))
+    ref = {k: v.reshape(shape) for k, v in acc.spectra().items()}
+    for k, g in zip(("coh", "inc", "tot"), ctx.spectrum()):
+        assert_parity(g, ref[k], what=f"variant {variant} {k}")
