@@ -5,7 +5,7 @@ import time
 import numpy as np
 import pytest
 
-from gpu_util import assert_parity, gpu_run, oracle_run, spectra_grid, to_dev
+from gpu_util import assert_parity, assert_sampled_bins, gpu_run, oracle_run, spectra_grid, to_dev
 from paper_1802_03972_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -120,6 +120,31 @@ def test_tune_keeps_parity():
     gpu_run(wl, range(5), ctx=ctx)
     ref = spectra_grid(oracle_run(wl, range(5)), wl)
     assert_parity(ctx.spectrum()[2], ref["tot"])
+
+
+def test_batched_job_mix_at_full_size_sampled_bins():
+    """The batched job mix at its full size, in the configuration the benchmark
+    times (64 jobs of 1e3-1e6 macro-particles on 64-1024 frequencies x 16-1024
+    directions, each round one persistent launch): two rounds of distinct steps,
+    then 4 sampled bins of every job against the oracle under the per-bin gate."""
+    specs = inputs.job_mix(64)
+    wls = [s.workload() for s in specs]
+    ctxs = [rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width) for wl in wls]
+    batch = rad.Batch(ctxs)
+    for r in range(2):
+        data = [dev_steps(wl, r) for wl in wls]
+        batch.accumulate([rad.make_step(st.n, *arrs, st.t, st.dt) for st, arrs in data])
+        batch.sync()
+    rng = np.random.default_rng(11)
+    for j, (wl, ctx) in enumerate(zip(wls, ctxs)):
+        got = dict(zip(("coh", "inc", "tot"), ctx.spectrum()))
+        bins = [(int(rng.integers(0, wl.dirs.shape[0])), int(rng.integers(0, wl.omega.shape[0])))
+                for _ in range(4)]
+        ref = oracle_run(wl, range(2), bins).spectra()
+        assert_sampled_bins(got, ref, bins, what=f"job {j}")
+    batch.close()
+    for c in ctxs:
+        c.close()
 
 
 @pytest.mark.parametrize("policy", [(0, 0), (1, 1), (2, 1_000_000), (3, 1_000_000), (4, 1_000_000)])

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import BIN_AMP, BIN_REL, assert_parity, to_dev
+from gpu_util import assert_parity, assert_sampled_bins, to_dev
 from paper_1802_03972_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -68,13 +68,8 @@ def test_insitu_scale_chunked_sampled_and_shapes(bunch):
     for st in bunch:
         acc.accumulate(st.r, st.beta, st.beta_dot, st.w, st.t, st.dt)
     for shape, got in ((oracle.FF_CIC, cic), (oracle.FF_TSC, tsc)):
-        ref = acc.spectra(shape, 0.1e-6)
-        for i, (d, o) in enumerate(bins):
-            for k, g in zip(("coh", "inc", "tot"), got):
-                m = np.abs(g[d]).max()
-                r = ref[k][i]
-                allowed = BIN_REL * r + 2.0 * BIN_AMP * np.sqrt(r * m) + BIN_AMP ** 2 * m
-                assert abs(g[d, o] - r) <= allowed, (shape, k, d, o, g[d, o], r)
+        assert_sampled_bins(dict(zip(("coh", "inc", "tot"), got)), acc.spectra(shape, 0.1e-6), bins,
+                            what=f"shape {shape}")
 
 
 def test_insitu_scale_mixed_vs_plain_fp64(bunch):
