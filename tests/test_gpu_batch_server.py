@@ -187,6 +187,34 @@ def test_server_results_equal_alone_and_in_the_mix(policy):
     srv.close()
 
 
+def test_served_job_mix_sampled_bins():
+    """Eight jobs of the serving mix at their full sizes (up to 1e6 particles
+    and 1024 x 32^2 bins) submitted together to a server with four slots under
+    the default policy, three steps each fed from device buffers: 4 sampled
+    bins of every result against the oracle under the per-bin gate."""
+    specs = inputs.job_mix(8, base_seed=5000, steps=(3, 3))
+    wls = [s.workload() for s in specs]
+    data = [[dev_steps(wl, s) for s in range(3)] for wl in wls]
+    srv = rad.Server(hbm_budget=64 << 30, max_slots=4)
+    ids = [srv.submit(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width, max_particles=wl.n_particles,
+                      max_queued=3) for wl in wls]
+    for j in range(len(wls)):
+        for st, arrs in data[j]:
+            step = rad.make_step(st.n, *arrs, st.t, st.dt)
+            deadline = time.time() + 60
+            while srv.feed(ids[j], step) != rad.RAD_OK and time.time() < deadline:
+                time.sleep(0.001)
+        srv.finish(ids[j])
+    rng = np.random.default_rng(12)
+    for j, wl in enumerate(wls):
+        coh, inc, tot, _ = srv.result(ids[j], wl.dirs.shape[0], wl.omega.shape[0], timeout=300)
+        bins = [(int(rng.integers(0, wl.dirs.shape[0])), int(rng.integers(0, wl.omega.shape[0])))
+                for _ in range(4)]
+        ref = oracle_run(wl, range(3), bins).spectra()
+        assert_sampled_bins({"coh": coh, "inc": inc, "tot": tot}, ref, bins, what=f"job {j}")
+    srv.close()
+
+
 def test_server_policy_arguments():
     srv = rad.Server(hbm_budget=1 << 30, max_slots=2)
     for bad in ((5, 10), (-1, 10), (1, 0), (2, -5), (3, 0), (4, 0)):
