@@ -44,7 +44,9 @@ VARIANT_NAMES = {0: "FP32 FMA, 256 threads x 2 omega, 3 CTAs/SM",
                  7: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads, 3 CTAs/SM, "
                     "two frequency passes per staged particle tile",
                  8: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads x 2 omega "
-                    "(64 per warp), 2 CTAs/SM"}
+                    "(64 per warp), 2 CTAs/SM",
+                 9: "tensor-core accumulation (mma.sync TF32 hi/lo), 256 threads x 2 omega "
+                    "(64 per warp), 2 CTAs/SM, phase cross terms by mma.sync"}
 # The accumulate kernel's sources: the kernel file and the headers its device code comes from.
 KERNEL_SRC = [os.path.join(ROOT, "paper_1802_03972_gb300", "csrc", f)
               for f in ("rad_accumulate.cu", "rad_stage.cuh", "rad_device.cuh", "rad_impl.h")]
@@ -771,7 +773,7 @@ def main():
                 for st in steps_host]
     upd = wl.updates_per_step()
     if args.wide_only:
-        tile = tuple(int(x) for x in args.tile.split(",")) if args.tile else (8, 512, 0)
+        tile = tuple(int(x) for x in args.tile.split(",")) if args.tile else (9, 512, 0)
         print(json.dumps({"wide_bunch": wide_leg(wl, tile, n_steps=args.steps)}), flush=True)
         return
     ctx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)

@@ -227,9 +227,10 @@ rad_status rad_state_merge(rad_ctx* ctx, const void* host_buf, size_t n);
  *            (4 blocks per SM).  Tensor-core accumulation (TF32 hi/lo), a warp per
  *            32 frequencies: 3 (3 blocks per SM), 4 (4 blocks per SM), 7 = 3 with
  *            each staged particle tile swept in two frequency passes; a warp per
- *            64 frequencies (2 frequencies per thread): 8 (2 blocks per SM, the
- *            default of a new context).  6 = FP32 with the literal sum, used by,
- *            and only by, RAD_FF_LITERAL contexts.
+ *            64 frequencies (2 frequencies per thread): 8 (2 blocks per SM) and 9
+ *            (as 8, with the phases' float-float cross terms formed by one more
+ *            MMA per block; the default of a new context).  6 = FP32 with the
+ *            literal sum, used by, and only by, RAD_FF_LITERAL contexts.
  *  omega_tile frequencies per tile: a multiple of 32 x frequencies per thread x
  *            passes, at most 256 x frequencies per thread x passes; directions
  *            per tile follow from the block's bin count.  RAD_EINVAL otherwise.

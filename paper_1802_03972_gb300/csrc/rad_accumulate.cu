@@ -64,10 +64,10 @@ using namespace dev;
 
 constexpr uint32_t kTf32Mask = 0xFFFFE000u;  // sign, exponent, 10 mantissa bits
 
-template <int THREADS, bool TC, bool LIT = false, int PASSES = 1>
+template <int THREADS, bool TC, bool LIT = false, int PASSES = 1, bool XT = false>
 struct Smem {
   static constexpr size_t raw_bytes = (size_t)THREADS * kRecFields * sizeof(float);
-  static constexpr size_t rec_bytes = (size_t)THREADS * (TC ? 40 : (LIT ? 64 : 48));
+  static constexpr size_t rec_bytes = (size_t)THREADS * (XT ? 84 : TC ? 40 : (LIT ? 64 : 48));
   static constexpr size_t l2_bytes = TC ? (size_t)THREADS * 16 * sizeof(float) * PASSES : 0;
   static constexpr size_t bytes = raw_bytes + 2 * rec_bytes + l2_bytes;
 };
@@ -87,6 +87,67 @@ __device__ __forceinline__ TileGeom tile_geom(const JobStatic& J, int tile, int 
   return g;
 }
 
+// A work item: its tile and particle chunk, and the chunking of that tile.
+// fine: the tile's index among the job's fine-chunked last tiles (TailPlan),
+// -1 for the others.
+struct ItemRef {
+  int tile, chunk, ck, n_chunks, fine;
+};
+
+// Item `local` of a job: the coarse tiles' items tile-major, then the fine
+// tiles' items tile-major.
+__device__ __forceinline__ ItemRef decode_item(const JobStatic& J, const JobCall& K,
+                                               long long local) {
+  ItemRef it;
+  const long long coarse = (long long)(J.n_tiles - K.tail_tiles) * K.n_chunks;
+  if (local < coarse) {
+    it.tile = (int)(local / K.n_chunks);
+    it.chunk = (int)(local - (long long)it.tile * K.n_chunks);
+    it.ck = K.ck;
+    it.n_chunks = K.n_chunks;
+    it.fine = -1;
+  } else {
+    const long long l = local - coarse;
+    it.fine = (int)(l / K.n_chunks_f);
+    it.tile = J.n_tiles - K.tail_tiles + it.fine;
+    it.chunk = (int)(l - (long long)it.fine * K.n_chunks_f);
+    it.ck = K.ck_f;
+    it.n_chunks = K.n_chunks_f;
+  }
+  return it;
+}
+
+// Where an item's partial sums live: component comp of chunk ch at
+// base[ch * chunk_stride + comp * comp_stride + bin offset].  Coarse tiles:
+// J.partials [chunk][comp][n_bins], the offset the bin; fine tiles:
+// J.partials_f [chunk][comp][tail_tiles][NT WT], the offset the bin's index
+// within the tile.  limit: the floats from base (index checks).
+struct PartMap {
+  float* base;
+  size_t chunk_stride, comp_stride;
+  long long limit;
+};
+__device__ __forceinline__ PartMap part_map(const JobStatic& J, const JobCall& K, const ItemRef& it,
+                                            const TileGeom& g) {
+  PartMap m;
+  if (it.fine < 0) {
+    m.base = J.partials;
+    m.comp_stride = (size_t)J.n_bins;
+    m.limit = (long long)J.chunk_cap * kComps * J.n_bins;
+  } else {
+    const size_t tb = (size_t)g.NT * g.WT;
+    m.base = J.partials_f + (size_t)it.fine * tb;
+    m.comp_stride = (size_t)K.tail_tiles * tb;
+    m.limit = J.fine_cap - (long long)it.fine * (long long)tb;
+  }
+  m.chunk_stride = (size_t)kComps * m.comp_stride;
+  return m;
+}
+__device__ __forceinline__ size_t part_bin(const JobStatic& J, const ItemRef& it, const TileGeom& g,
+                                           int d, int o) {
+  return it.fine < 0 ? (size_t)d * J.n_omega + o : (size_t)(d - g.d0) * g.WT + (o - g.o0);
+}
+
 // Compensated (Kahan) add of x into sum with compensation cmp.
 __device__ __forceinline__ void kahan_add(float* sum, float* cmp, float x) {
   const float y = __fsub_rn(x, *cmp);
@@ -97,13 +158,13 @@ __device__ __forceinline__ void kahan_add(float* sum, float* cmp, float x) {
 
 // Arrival counter of the bin tile; true for the last work item of this call.
 template <int THREADS>
-__device__ __forceinline__ bool last_arrival(const JobStatic& J, const JobCall& K, int tile,
-                                             int* s_flag) {
+__device__ __forceinline__ bool last_arrival(const JobStatic& J, const ItemRef& it, int* s_flag) {
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    const int tile = it.tile;
     const unsigned prev = atomicAdd(&J.tile_cnt[tile], 1u);
-    *s_flag = (prev == (unsigned)(K.n_chunks - 1));
+    *s_flag = (prev == (unsigned)(it.n_chunks - 1));
     if (*s_flag) J.tile_cnt[tile] = 0u;  // ready for the next call
     __threadfence();
   }
@@ -119,20 +180,25 @@ __device__ __forceinline__ void discard_l2_line(const void* p) {
 
 // The partial sums of a tile are dead once the last arrival has added them up,
 // and every call rewrites each slot before reading it.  Dropping their L2
-// lines saves the write-back to DRAM.  Arrays: n_arrays consecutive [n_bins]
-// float arrays from base; only whole lines inside the tile's bin range of each
-// direction are dropped, so the neighbouring tiles' partials are untouched.
+// lines saves the write-back to DRAM.  Arrays: n_arrays arrays from base, one
+// every `stride` floats, each laid out as [n_bins] (fine: false) or as the
+// fine tiles' [tail_tiles][NT WT] with base at this tile (fine: true); only
+// whole lines inside the tile's bins of each direction are dropped, so the
+// neighbouring tiles' partials are untouched.
 template <int THREADS>
-__device__ __forceinline__ void discard_tile_partials(const float* base, long long n_arrays,
-                                                      const JobStatic& J, const TileGeom& g) {
+__device__ __forceinline__ void discard_tile_partials(const float* base, size_t stride,
+                                                      long long n_arrays, const JobStatic& J,
+                                                      const TileGeom& g, bool fine) {
   // Four arrays per warp, eight lanes per array: a 256-bin row is 8 lines.
   const int sub = threadIdx.x >> 3, l8 = threadIdx.x & 7;
   const int n_om = J.n_omega, o1 = min(g.o0 + g.WT, n_om);
   for (long long arr = sub; arr < n_arrays; arr += THREADS / 8) {
+    const float* ap = base + (size_t)arr * stride;
     for (int dl = 0; dl < g.NT; ++dl) {
       const int d = g.d0 + dl;
       if (d >= J.n_dir) break;
-      const float* rp = base + (size_t)arr * J.n_bins + (size_t)d * n_om;
+      // rp + o: the partial of bin (d, o)
+      const float* rp = fine ? ap + (size_t)dl * g.WT - g.o0 : ap + (size_t)d * n_om;
       const uintptr_t a0 = reinterpret_cast<uintptr_t>(rp + g.o0);
       const uintptr_t a1 = reinterpret_cast<uintptr_t>(rp + o1);
       for (uintptr_t line = ((a0 + 127) & ~(uintptr_t)127) + (uintptr_t)l8 * 128; line + 128 <= a1;
@@ -146,23 +212,33 @@ __device__ __forceinline__ void discard_tile_partials(const float* base, long lo
 // order, rotate by e^{i omega tau_ref(n)} and add into the state (Kahan).
 // DISCARD: then drop the partials' L2 lines (tensor-core variants; the FP32
 // variants measured slower with it and keep the write-back).
+// Whether an item's chunks fit the partial-sum buffer it writes.
+__device__ __forceinline__ bool part_fits(const JobStatic& J, const ItemRef& it, const PartMap& m) {
+  return it.fine < 0 ? it.n_chunks <= J.chunk_cap
+                     : J.fine_cap >= (long long)it.n_chunks * (long long)m.chunk_stride;
+}
+
 template <int THREADS, bool DISCARD>
-__device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall& K, int tile) {
+__device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall& K,
+                                              const ItemRef& it) {
+  const int tile = it.tile;
   const TileGeom g = tile_geom(J, tile, THREADS);
+  const PartMap m = part_map(J, K, it, g);
   const int nb = J.n_bins, n_om = J.n_omega;
-  if (!bounds_ok(K.n_chunks <= J.chunk_cap && tile < J.n_tiles, J.status)) return;
+  if (!bounds_ok(part_fits(J, it, m) && tile < J.n_tiles, J.status)) return;
   for (int i = threadIdx.x; i < g.NT * g.WT; i += THREADS) {
     const int dl = i / g.WT;
     const int d = g.d0 + dl, o = g.o0 + (i - dl * g.WT);
     if (d >= J.n_dir || o >= n_om) continue;
     const int bin = d * n_om + o;
+    const size_t off = part_bin(J, it, g, d, o);
     float s[kComps];
 #pragma unroll
     for (int c = 0; c < kComps; ++c) s[c] = 0.0f;
-    for (int ch = 0; ch < K.n_chunks; ++ch) {
-      const float* pc = J.partials + (size_t)ch * kComps * nb;
+    for (int ch = 0; ch < it.n_chunks; ++ch) {
+      const float* pc = m.base + (size_t)ch * m.chunk_stride;
 #pragma unroll
-      for (int c = 0; c < kComps; ++c) s[c] += __ldcg(&pc[(size_t)c * nb + bin]);
+      for (int c = 0; c < kComps; ++c) s[c] += __ldcg(&pc[(size_t)c * m.comp_stride + off]);
     }
     const double* nd = J.dirs + 3 * d;
     const double tref = J.ref[3] - (nd[0] * J.ref[0] + nd[1] * J.ref[1] + nd[2] * J.ref[2]) * kInvC;
@@ -178,9 +254,9 @@ __device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall&
       kahan_add(&st[(size_t)c * nb + bin], &st[(size_t)(kComps + c) * nb + bin], re);
       kahan_add(&st[(size_t)(c + 1) * nb + bin], &st[(size_t)(kComps + c + 1) * nb + bin], im);
     }
-    if (J.literal) {
+    if (J.literal) {  // (literal contexts run an FP32 variant: never fine tiles)
       float p[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int ch = 0; ch < K.n_chunks; ++ch) {
+      for (int ch = 0; ch < it.n_chunks; ++ch) {
         const float* pc = J.partials_p + (size_t)ch * 4 * nb;
 #pragma unroll
         for (int c = 0; c < 4; ++c) p[c] += __ldcg(&pc[(size_t)c * nb + bin]);
@@ -197,8 +273,11 @@ __device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall&
   }
   if constexpr (DISCARD) {
     __syncthreads();  // every thread's reads of the partials are done
-    discard_tile_partials<THREADS>(J.partials, (long long)K.n_chunks * kComps, J, g);
-    if (J.literal) discard_tile_partials<THREADS>(J.partials_p, (long long)K.n_chunks * 4, J, g);
+    discard_tile_partials<THREADS>(m.base, m.comp_stride, (long long)it.n_chunks * kComps, J, g,
+                                   it.fine >= 0);
+    if (J.literal)
+      discard_tile_partials<THREADS>(J.partials_p, (size_t)nb, (long long)it.n_chunks * 4, J, g,
+                                     false);
   }
 }
 
@@ -228,9 +307,10 @@ __device__ __forceinline__ void issue_tile(const JobStatic& J, long long k0, int
 // LIT: also the paper's literal sum P_i += sqrt(w) dt a_i g e^{i phi} with
 // g = sqrt(1 + (w - 1) f(omega)^2), i.e. F_k(omega) dt a_i (Eq. 13 with Eq. 12).
 template <int THREADS, int W, int UNROLL, bool LIT = false, bool WIDE = false>
-__device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCall& K, int tile,
-                                                 int chunk, unsigned char* __restrict__ smem,
+__device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCall& K,
+                                                 const ItemRef& item, unsigned char* __restrict__ smem,
                                                  uint64_t* bar, uint32_t& phase, int* s_flag) {
+  const int tile = item.tile, chunk = item.chunk;
   constexpr int NP = W / 2;
   constexpr int REC = LIT ? 4 : 3;                 // float4 per record
   constexpr int NC = kComps + (LIT ? 4 : 0);       // accumulated components per frequency
@@ -271,8 +351,8 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
     for (int c = 0; c < NC; ++c) acc1[p][c] = acc2[p][c] = make_float2(0.f, 0.f);
   const float2 kOne = make_float2(1.0f, 1.0f);
 
-  const long long k_begin = (long long)chunk * K.ck;
-  const long long k_end = min(k_begin + (long long)K.ck, K.n);
+  const long long k_begin = (long long)chunk * item.ck;
+  const long long k_end = min(k_begin + (long long)item.ck, K.n);
   const int n_kt = (int)((k_end - k_begin + g.KT - 1) / g.KT);
   // Whole tiles are copied: k_begin is a multiple of KT and the record buffer
   // holds at least round_up(n, 256) particles, so every copy stays in bounds.
@@ -422,18 +502,20 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
 
   // Partial sums of this work item.
   const int nb = J.n_bins;
-  float* part = J.partials + (size_t)chunk * kComps * nb;
+  const PartMap pm = part_map(J, K, item, g);
+  float* part = pm.base + (size_t)chunk * pm.chunk_stride;
   if (my_d_raw < J.n_dir) {
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int o = om_first + 2 * p + e;
-        if (o < n_om && bounds_ok(chunk < J.chunk_cap, J.status)) {
+        if (o < n_om && bounds_ok(chunk < item.n_chunks && part_fits(J, item, pm), J.status)) {
           const int bin = my_d * n_om + o;
+          const size_t off = part_bin(J, item, g, my_d, o);
 #pragma unroll
           for (int c = 0; c < kComps; ++c)
-            part[(size_t)c * nb + bin] = e ? acc2[p][c].y : acc2[p][c].x;
+            part[(size_t)c * pm.comp_stride + off] = e ? acc2[p][c].y : acc2[p][c].x;
           if (LIT) {
             float* pp = J.partials_p + (size_t)chunk * 4 * nb;
 #pragma unroll
@@ -443,7 +525,7 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
         }
       }
   }
-  if (last_arrival<THREADS>(J, K, tile, s_flag)) tile_epilogue<THREADS, false>(J, K, tile);
+  if (last_arrival<THREADS>(J, item, s_flag)) tile_epilogue<THREADS, false>(J, K, item);
   return true;
 }
 
@@ -464,6 +546,29 @@ __device__ __forceinline__ void split_pair(float2 v, uint32_t& h0, uint32_t& h1,
   h0 = tf32_hi(v.x);
   h1 = tf32_hi(v.y);
   lo = __fadd2_rn(v, make_float2(-__uint_as_float(h0), -__uint_as_float(h1)));
+}
+
+// The TF32 value nearest to x (ties away from zero), as bits.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return y;
+}
+
+// x ~ hi + lo, both TF32 values, |x - hi - lo| <= 2^-22 |x|.
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(__fsub_rn(x, __uint_as_float(hi)));
+}
+
+// d = A B (m16n8k8 TF32, zero accumulator).
+__device__ __forceinline__ void mma_tf32_zero(float d[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                              uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%10,%10,%10,%10};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(0.0f));
 }
 
 // One 16-frequency x 8-particle MMA block: pA / pB are the phases of the
@@ -489,15 +594,19 @@ __device__ __forceinline__ void tc_block(float2 pA, float2 pB, uint32_t b0, uint
            __float_as_uint(sbL.y), b0, b1);
 }
 
-// Warp layout: warp w handles direction d0 + w / (WT/32) and 32 frequencies
-// (two 16-row MMA blocks) starting at o0 + 32 (w % (WT/32)).
-template <int THREADS, int PASSES, int NB, bool WIDE = false>
-__device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCall& K, int tile,
-                                                int chunk, unsigned char* __restrict__ smem,
+// Warp layout: warp w handles direction d0 + w / (WT/(16 NB)) and 16 NB
+// frequencies (NB 16-row MMA blocks) starting at o0 + 16 NB (w % (WT/(16 NB))).
+// XT: the phases' cross terms 2pi (omega_lo th + omega_hi tl) come from one
+// more MMA per block (below), and the phase arithmetic is packed over particle
+// pairs instead of frequency pairs.
+template <int THREADS, int PASSES, int NB, bool WIDE = false, bool XT = false>
+__device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCall& K,
+                                                const ItemRef& item, unsigned char* __restrict__ smem,
                                                 uint64_t* bar, uint32_t& phase, int* s_flag) {
+  const int tile = item.tile, chunk = item.chunk;
   // NB: 16-frequency blocks per warp; GQ: second-level float4 groups per pass
   constexpr int GQ = 2 * NB;
-  using S = Smem<THREADS, true, false, PASSES * NB / 2>;
+  using S = Smem<THREADS, true, false, PASSES * NB / 2, XT>;
   float* raw = reinterpret_cast<float*>(smem);
   const TileGeom g = tile_geom(J, tile, THREADS);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -517,13 +626,38 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
   constexpr bool wide = WIDE;
 
   float2 omh[NB], wh[NB], wl[NB];
+  // XT: omega/2pi (hi) of rows r and r + 8 of each block, each in both halves
+  // of a pair, and the A fragment of the cross-term product.  That product has
+  // eight terms t (A columns, B rows), with x ~ x_hi + x_lo split into TF32
+  // values:  t = 0..7: wl_hi th_hi, wl_hi th_lo, wl_lo th_hi, wh_hi tl_hi,
+  // wh_hi tl_lo, wh_lo tl_hi, wl_lo th_lo, wh_lo tl_lo  (wh, wl: 2pi omega hi
+  // and lo in radians; th, tl: the particle's dtau hi and lo), which sum to
+  // wl th + wh tl.
+  float2 omr[NB], omr8[NB];
+  uint32_t xa[NB][4];
   auto load_omega = [&](int o_warp) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int i0 = min(o_warp + 16 * b + r, n_om - 1), i1 = min(o_warp + 16 * b + r + 8, n_om - 1);
-      omh[b] = make_float2(__ldg(J.om_tab + i0), __ldg(J.om_tab + i1));
-      wh[b] = make_float2(__ldg(J.om_tab + n_om + i0), __ldg(J.om_tab + n_om + i1));
-      wl[b] = make_float2(__ldg(J.om_tab + 2 * n_om + i0), __ldg(J.om_tab + 2 * n_om + i1));
+      if constexpr (XT) {
+        const float h0 = __ldg(J.om_tab + i0), h1 = __ldg(J.om_tab + i1);
+        omr[b] = make_float2(h0, h0);
+        omr8[b] = make_float2(h1, h1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = h ? i1 : i0;
+          uint32_t whh, whl, wlh, wll;
+          split_tf32(__ldg(J.om_tab + n_om + i), whh, whl);
+          split_tf32(__ldg(J.om_tab + 2 * n_om + i), wlh, wll);
+          // a0/a1: column c of rows r / r + 8; a2/a3: column c + 4.
+          xa[b][h] = c == 3 ? whh : (c == 2 ? wll : wlh);
+          xa[b][2 + h] = c == 0 ? whh : (c == 2 ? wll : whl);
+        }
+      } else {
+        omh[b] = make_float2(__ldg(J.om_tab + i0), __ldg(J.om_tab + i1));
+        wh[b] = make_float2(__ldg(J.om_tab + n_om + i0), __ldg(J.om_tab + n_om + i1));
+        wl[b] = make_float2(__ldg(J.om_tab + 2 * n_om + i0), __ldg(J.om_tab + 2 * n_om + i1));
+      }
     }
   };
   load_omega(o_warp0);
@@ -538,8 +672,8 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
 #pragma unroll
   for (int v = 0; v < GQ * PASSES; ++v) l2[v * THREADS + threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-  const long long k_begin = (long long)chunk * K.ck;
-  const long long k_end = min(k_begin + (long long)K.ck, K.n);
+  const long long k_begin = (long long)chunk * item.ck;
+  const long long k_end = min(k_begin + (long long)item.ck, K.n);
   const int n_kt = (int)((k_end - k_begin + g.KT - 1) / g.KT);
   if (threadIdx.x == 0) issue_tile(J, k_begin, g.KT, raw, bar);
   for (int it = 0; it < n_kt; ++it) {
@@ -548,6 +682,14 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
     unsigned char* recb = smem + S::raw_bytes + (size_t)(it & 1) * S::rec_bytes;
     float2* tau2 = reinterpret_cast<float2*>(recb);                     // [NT][KT]
     float* ampb = reinterpret_cast<float*>(recb + (size_t)THREADS * 8);  // [NT][KT][8]
+    // XT records: dtau hi [NT][KT]; the cross-term B rows [NT][KT][8] as four
+    // pairs (terms c, c + 4), pair c of particle p at position c ^ 2 ((p >> 2) & 1)
+    // (lane c reads its pair with one 8-byte load); the amplitudes' hi/lo parts
+    // [NT][KT][12], 8 used.  The swizzle and the 12-word stride keep both the
+    // stage-1 stores and the loop's loads free of bank conflicts.
+    float* xth = reinterpret_cast<float*>(recb);
+    float* xrt = reinterpret_cast<float*>(recb + (size_t)THREADS * 4);
+    float* xam = reinterpret_cast<float*>(recb + (size_t)THREADS * 36);
     const bool landed = mbar_wait(bar, phase);
     phase ^= 1u;
     bool slow = false;
@@ -558,13 +700,31 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
                                tl, a);
       // Particles past kn are zero padding of the last 8-particle MMA step.
       const int slot = s1_dl * g.KT + s1_kk;
-      tau2[slot] = make_float2(th, tl);
-      float4* ap = reinterpret_cast<float4*>(ampb + (size_t)slot * 8);
       const uint32_t h0 = tf32_hi(a[0]), h1 = tf32_hi(a[1]), h2 = tf32_hi(a[2]), h3 = tf32_hi(a[3]);
-      ap[0] = make_float4(__uint_as_float(h0), __uint_as_float(h1), __uint_as_float(h2),
-                          __uint_as_float(h3));
-      ap[1] = make_float4(a[0] - __uint_as_float(h0), a[1] - __uint_as_float(h1),
-                          a[2] - __uint_as_float(h2), a[3] - __uint_as_float(h3));
+      if constexpr (XT) {
+        xth[slot] = th;
+        uint32_t thh, thl, tlh, tll;
+        split_tf32(th, thh, thl);
+        split_tf32(tl, tlh, tll);
+        float4* rp = reinterpret_cast<float4*>(xrt + (size_t)slot * 8);
+        const int sw = (s1_kk >> 2) & 1;  // pairs 0, 1 and 2, 3 swap places
+        rp[sw] = make_float4(__uint_as_float(thh), __uint_as_float(tll), __uint_as_float(thl),
+                             __uint_as_float(tlh));
+        rp[sw ^ 1] = make_float4(__uint_as_float(thh), __uint_as_float(thl),
+                                 __uint_as_float(tlh), __uint_as_float(tll));
+        float4* ap = reinterpret_cast<float4*>(xam + (size_t)slot * 12);
+        ap[0] = make_float4(__uint_as_float(h0), __uint_as_float(h1), __uint_as_float(h2),
+                            __uint_as_float(h3));
+        ap[1] = make_float4(a[0] - __uint_as_float(h0), a[1] - __uint_as_float(h1),
+                            a[2] - __uint_as_float(h2), a[3] - __uint_as_float(h3));
+      } else {
+        tau2[slot] = make_float2(th, tl);
+        float4* ap = reinterpret_cast<float4*>(ampb + (size_t)slot * 8);
+        ap[0] = make_float4(__uint_as_float(h0), __uint_as_float(h1), __uint_as_float(h2),
+                            __uint_as_float(h3));
+        ap[1] = make_float4(a[0] - __uint_as_float(h0), a[1] - __uint_as_float(h1),
+                            a[2] - __uint_as_float(h2), a[3] - __uint_as_float(h3));
+      }
     }
     const int flags = __syncthreads_or((slow ? 1 : 0) | (landed ? 0 : 2));
     if (flags & 2) {
@@ -577,6 +737,18 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
     if (threadIdx.x == 0 && it + 1 < n_kt) issue_tile(J, kt + g.KT, g.KT, raw, bar);
     const float2* tw = tau2 + my_dl * g.KT;
     const float* aw = ampb + (size_t)my_dl * g.KT * 8;
+    const float* xtw = xth + my_dl * g.KT;
+    const float* xrw = xrt + (size_t)my_dl * g.KT * 8;
+    const float* xaw = xam + (size_t)my_dl * g.KT * 12;
+    // this lane's cross-term pair within particle kk + r's row (kk % 8 == 0)
+    const int xr_off = 2 * (c ^ ((r >> 1) & 2));
+    // XT, the 8-particle step at kk: the main product's k = c and k = c + 4 are
+    // particles kk + 2c and kk + 2c + 1 (the columns of the cross-term result
+    // this lane holds).
+    auto xamp = [&](int kk) {
+      return make_uint2(__float_as_uint(xaw[(kk + 2 * c) * 12 + r]),
+                        __float_as_uint(xaw[(kk + 2 * c + 1) * 12 + r]));
+    };
     const int kn8 = (kn + 7) & ~7;
 #pragma unroll 1
     for (int ps = 0; ps < PASSES; ++ps) {
@@ -588,6 +760,22 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
         auto fast_loop = [&](const int kend) {
 #pragma unroll kUnroll
           for (int kk = 0; kk < kend; kk += 8) {
+            if constexpr (XT) {
+              const float2 th2 = *reinterpret_cast<const float2*>(xtw + kk + 2 * c);
+              const uint2 rt = *reinterpret_cast<const uint2*>(xrw + (size_t)(kk + r) * 8 + xr_off);
+              const uint2 bb = xamp(kk);
+#pragma unroll
+              for (int b = 0; b < NB; ++b) {
+                // cr: rows r, r + 8 x particles kk + 2c, kk + 2c + 1
+                float cr[4];
+                mma_tf32_zero(cr, xa[b][0], xa[b][1], xa[b][2], xa[b][3], rt.x, rt.y);
+                const float2 p0 = phase2x(omr[b], th2, make_float2(cr[0], cr[1]));
+                const float2 p8 = phase2x(omr8[b], th2, make_float2(cr[2], cr[3]));
+                tc_block(make_float2(p0.x, p8.x), make_float2(p0.y, p8.y), bb.x, bb.y, dre[b],
+                         dim[b]);
+              }
+              continue;
+            }
             const float2 tA = tw[kk + c], tB = tw[kk + c + 4];
             const uint32_t b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
             const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
@@ -617,9 +805,27 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
           omt[b][1] = J.om_turns[min(o_warp + 16 * b + r + 8, n_om - 1)];
         }
         for (int kk = 0; kk < kn8; kk += 8) {
-          const float2 tA = tw[kk + c], tB = tw[kk + c + 4];
-          const uint32_t b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
-          const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
+          float2 tA, tB;
+          uint32_t b0, b1;
+          if constexpr (XT) {
+            // particles kk + 2c and kk + 2c + 1; tl = tl_hi + tl_lo (terms 3, 7:
+            // pair 3, at position 3 ^ 2 ((p >> 2) & 1))
+            const int pa = kk + 2 * c;
+            auto tl_of = [&](int p) {
+              const float* q = xrw + (size_t)p * 8 + 2 * (3 ^ (((p >> 2) & 1) << 1));
+              return q[0] + q[1];
+            };
+            tA = make_float2(xtw[pa], tl_of(pa));
+            tB = make_float2(xtw[pa + 1], tl_of(pa + 1));
+            const uint2 bb = xamp(kk);
+            b0 = bb.x;
+            b1 = bb.y;
+          } else {
+            tA = tw[kk + c];
+            tB = tw[kk + c + 4];
+            b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
+            b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
+          }
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
             const float2 pA = make_float2(phase_wide(omt[b][0], tA.x, tA.y, tau_g),
@@ -658,6 +864,13 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
             }
         }
       }
+      // Second level: after every particle tile the tile sums join the chunk
+      // sums in shared memory, so the MMA accumulators never sum more than one
+      // tile.  Longer runs would be faster (LWFA workload, variant 9: a flush
+      // every second tile 0.2 % and every fourth 0.5 % less time per step) but
+      // the MMA's FP32 accumulation error grows with the run's length: at every
+      // fourth tile a 5000-particle workload read 1.3e-5 of row error against
+      // the oracle (gate 1e-5), about four times that of a flush every tile.
       float4* l2p = l2 + ps * GQ * THREADS + threadIdx.x;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
@@ -677,8 +890,8 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
   // The D fragment holds rows (r, r+8) and columns (2c, 2c+1); columns 0-3 are
   // the hi parts of (U.e1, U.e2, V.e1, V.e2), columns 4-7 the lo parts: lane c
   // (c < 2) adds lane c+2's values.
-  const int nb = J.n_bins;
-  float* part = J.partials + (size_t)chunk * kComps * nb;
+  const PartMap pm = part_map(J, K, item, g);
+  float* part = pm.base + (size_t)chunk * pm.chunk_stride;
 #pragma unroll 1
   for (int ps = 0; ps < PASSES; ++ps)
 #pragma unroll
@@ -692,13 +905,14 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
       const float im = lim + __shfl_xor_sync(0xffffffffu, lim, 2);
       const int o = o_warp0 + ps * PW + 16 * b + r + ((e >> 1) << 3);
       const int j = 2 * c + (e & 1);  // amplitude column
-      if (c < 2 && my_d_raw < J.n_dir && o < n_om && bounds_ok(chunk < J.chunk_cap, J.status)) {
-        const int bin = my_d * n_om + o;
-        part[(size_t)(2 * j) * nb + bin] = re;
-        part[(size_t)(2 * j + 1) * nb + bin] = im;
+      if (c < 2 && my_d_raw < J.n_dir && o < n_om &&
+          bounds_ok(chunk < item.n_chunks && part_fits(J, item, pm), J.status)) {
+        const size_t off = part_bin(J, item, g, my_d, o);
+        part[(size_t)(2 * j) * pm.comp_stride + off] = re;
+        part[(size_t)(2 * j + 1) * pm.comp_stride + off] = im;
       }
     }
-  if (last_arrival<THREADS>(J, K, tile, s_flag)) tile_epilogue<THREADS, true>(J, K, tile);
+  if (last_arrival<THREADS>(J, item, s_flag)) tile_epilogue<THREADS, true>(J, K, item);
   return true;
 }
 
@@ -706,7 +920,8 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
 // wide calls (exits at once when no job of the launch is wide).  The two run
 // one after the other on the same stream, each with its own item counter, so
 // the common path keeps its register allocation free of the wide-call code.
-template <int THREADS, int W, int MINB, bool TC, bool LIT, int PASSES = 1, bool WIDE = false>
+template <int THREADS, int W, int MINB, bool TC, bool LIT, int PASSES = 1, bool WIDE = false,
+          bool XT = false>
 __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a) {
   // Whether any job of the launch is wide is final before either kernel starts:
   // the wide one leaves at once without, and the ordinary one then takes every
@@ -742,18 +957,14 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     const JobStatic& J = a.js[j];
     if (any_wide && (J.wide_flag != nullptr && *J.wide_flag != 0) != WIDE) continue;  // the other kernel's
     const JobCall K = a.use_inline ? a.inline_call : a.jc[j];
-    const long long local = item - K.item_begin;
     // Tile-major order: the chunks of one tile run close together in time, so
     // their partial sums are still in L2 when the tile's last arrival reads them.
-    const int chunk = (int)(local % K.n_chunks);
-    const int tile = (int)(local / K.n_chunks);
+    const ItemRef it = decode_item(J, K, item - K.item_begin);
     bool ok;
     if constexpr (TC)
-      ok = process_item_tc<THREADS, PASSES, 2 * W, WIDE>(J, K, tile, chunk, smem, &bar, phase,
-                                                         &s_flag);
+      ok = process_item_tc<THREADS, PASSES, 2 * W, WIDE, XT>(J, K, it, smem, &bar, phase, &s_flag);
     else
-      ok = process_item_fma<THREADS, W, 8, LIT, WIDE>(J, K, tile, chunk, smem, &bar, phase,
-                                                      &s_flag);
+      ok = process_item_fma<THREADS, W, 8, LIT, WIDE>(J, K, it, smem, &bar, phase, &s_flag);
     if (!ok) break;
   }
   if (a.prof_clk && threadIdx.x == 0) {
@@ -762,38 +973,38 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
   }
 }
 
-template <int T, int W, int MINB, bool TC, bool LIT, int P = 1>
+template <int T, int W, int MINB, bool TC, bool LIT, int P = 1, bool XT = false>
 cudaError_t launch_acc(const LaunchArgs& a, int grid, cudaStream_t s) {
-  const size_t smem = Smem<T, TC, LIT, TC ? P * W : P>::bytes;
+  const size_t smem = Smem<T, TC, LIT, TC ? P * W : P, XT>::bytes;
   // The shared-memory opt-in is per kernel and device, and idempotent.
   static std::atomic<bool> attr_set[kMaxDevices];
   const int dev = current_device();
   if (dev < 0 || dev >= kMaxDevices || !attr_set[dev].load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P, false>,
+    cudaError_t e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P, false, XT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P, true>,
+      e = cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P, true, XT>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < kMaxDevices) attr_set[dev].store(true, std::memory_order_release);
   }
-  accumulate_kernel<T, W, MINB, TC, LIT, P, false><<<grid, T, smem, s>>>(a);
+  accumulate_kernel<T, W, MINB, TC, LIT, P, false, XT><<<grid, T, smem, s>>>(a);
   count_launches(1);
   if (a.any_wide != nullptr) {
-    accumulate_kernel<T, W, MINB, TC, LIT, P, true><<<grid, T, smem, s>>>(a);
+    accumulate_kernel<T, W, MINB, TC, LIT, P, true, XT><<<grid, T, smem, s>>>(a);
     count_launches(1);
   }
   return cudaGetLastError();
 }
 
-template <int T, int W, int MINB, bool TC, bool LIT, int P = 1>
+template <int T, int W, int MINB, bool TC, bool LIT, int P = 1, bool XT = false>
 int blocks_per_sm() {
   int nb = 0;
-  const size_t smem = Smem<T, TC, LIT, TC ? P * W : P>::bytes;
-  cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P, false>,
+  const size_t smem = Smem<T, TC, LIT, TC ? P * W : P, XT>::bytes;
+  cudaFuncSetAttribute(accumulate_kernel<T, W, MINB, TC, LIT, P, false, XT>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accumulate_kernel<T, W, MINB, TC, LIT, P, false>, T,
-                                                    smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &nb, accumulate_kernel<T, W, MINB, TC, LIT, P, false, XT>, T, smem) != cudaSuccess ||
       nb < 1)
     nb = 1;
   return nb;
@@ -805,7 +1016,8 @@ int blocks_per_sm() {
 // 3 tensor-core 256 (3 CTAs/SM), 4 tensor-core 256 (4 CTAs/SM), 5 FP32 256x2 (4 CTAs/SM),
 // 6 FP32 256x2 with the literal sum (2 CTAs/SM), 7 tensor-core 256 sweeping each staged
 // particle tile in two frequency passes, 8 tensor-core 256 with four 16-frequency blocks
-// per warp (512 frequencies per tile, 2 CTAs/SM).
+// per warp (512 frequencies per tile, 2 CTAs/SM), 9 as 8 with the phases' cross
+// terms on tensor cores.
 size_t accumulate_smem_bytes(int variant) {
   switch (variant) {
     case 2: return Smem<128, false>::bytes;
@@ -814,6 +1026,7 @@ size_t accumulate_smem_bytes(int variant) {
     case 6: return Smem<256, false, true>::bytes;
     case 7:
     case 8: return Smem<256, true, false, 2>::bytes;
+    case 9: return Smem<256, true, false, 2, true>::bytes;
     default: return Smem<256, false>::bytes;
   }
 }
@@ -837,6 +1050,7 @@ int accumulate_blocks_per_sm(int variant) {
     case 6: nb = blocks_per_sm<256, 2, 2, false, true>(); break;
     case 7: nb = blocks_per_sm<256, 1, 3, true, false, 2>(); break;
     case 8: nb = blocks_per_sm<256, 2, 2, true, false>(); break;
+    case 9: nb = blocks_per_sm<256, 2, 2, true, false, 1, true>(); break;
     default: nb = blocks_per_sm<256, 2, 3, false, false>(); break;
   }
   if (cache) cached[dev][variant].store(nb, std::memory_order_relaxed);
@@ -853,6 +1067,7 @@ cudaError_t launch_accumulate(int variant, const LaunchArgs& a, int grid, cudaSt
     case 6: return launch_acc<256, 2, 2, false, true>(a, grid, s);
     case 7: return launch_acc<256, 1, 3, true, false, 2>(a, grid, s);
     case 8: return launch_acc<256, 2, 2, true, false>(a, grid, s);
+    case 9: return launch_acc<256, 2, 2, true, false, 1, true>(a, grid, s);
     default: return launch_acc<256, 2, 3, false, false>(a, grid, s);
   }
 }

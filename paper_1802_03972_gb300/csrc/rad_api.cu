@@ -172,7 +172,7 @@ rad_status upload_static(rad_ctx* c) {
                                        cudaMemcpyHostToDevice, c->stream));
 }
 
-rad_status ensure_capacity(rad_ctx* c, long long n, int n_chunks) {
+rad_status ensure_capacity(rad_ctx* c, long long n, int n_chunks, long long fine_floats) {
   bool changed = false;
   if (n > c->h_js.n_cap) {
     long long cap = std::max(n, c->h_js.n_cap * 3 / 2);
@@ -223,6 +223,21 @@ rad_status ensure_capacity(rad_ctx* c, long long n, int n_chunks) {
       }
     }
     c->h_js.chunk_cap = cap;
+    changed = true;
+  }
+  if (fine_floats > c->h_js.fine_cap) {
+    const long long cap = std::max(fine_floats, c->h_js.fine_cap * 3 / 2);
+    if (c->h_js.partials_f) {
+      cudaStreamSynchronize(c->stream);
+      cudaFree(c->h_js.partials_f);
+      c->h_js.partials_f = nullptr;
+    }
+    rad_status s = cuda_check(c, dmalloc(&c->h_js.partials_f, (size_t)cap));
+    if (s != RAD_OK) {
+      c->h_js.fine_cap = 0;
+      return s;
+    }
+    c->h_js.fine_cap = cap;
     changed = true;
   }
   return changed ? upload_static(c) : RAD_OK;
@@ -291,7 +306,9 @@ rad_status enqueue_accumulate(rad_ctx* c, long long n, const double* r, const do
   const int variant = c->tile.variant;
   const int ck = auto_chunk(c, variant, n, c->h_js.n_tiles);
   const int n_chunks = (int)((n + ck - 1) / ck);
-  rad_status s = ensure_capacity(c, n, n_chunks);
+  const TailPlan tail = tail_plan(variant_tensor_core(variant) && !c->h_js.literal, n,
+                                  c->h_js.n_tiles, ck, n_chunks, resident_ctas(variant));
+  rad_status s = ensure_capacity(c, n, n_chunks, tail.fine_floats(c->h_js.nt * c->h_js.wt));
   if (s != RAD_OK) return s;
   LaunchArgs a;
   memset(&a, 0, sizeof(a));
@@ -299,7 +316,7 @@ rad_status enqueue_accumulate(rad_ctx* c, long long n, const double* r, const do
   a.jc = nullptr;
   a.n_jobs = 1;
   a.use_inline = 1;
-  a.n_items = (long long)c->h_js.n_tiles * n_chunks;
+  a.n_items = tail.items(c->h_js.n_tiles, n_chunks);
   a.item_counter = c->d_counter;  // [0], [1]: item counters; [2]: the wide flag
   // A call of at most one sorted group is never wide (the pre-pass does not
   // flag it): it needs neither the wide-call kernels nor the second kernel.
@@ -314,6 +331,9 @@ rad_status enqueue_accumulate(rad_ctx* c, long long n, const double* r, const do
   K.dt = dt;
   K.ck = ck;
   K.n_chunks = n_chunks;
+  K.tail_tiles = tail.tiles;
+  K.ck_f = tail.ck;
+  K.n_chunks_f = tail.n_chunks;
   K.item_begin = 0;
   K.block_begin = 0;
   s = cuda_check(c, cudaMemsetAsync(c->d_counter, 0, kCounterWords * sizeof(unsigned long long),
@@ -544,7 +564,7 @@ void rad_destroy(rad_ctx* c) {
                   c->d_status, c->d_counter, c->d_js, c->d_spec, c->d_state, c->d_state64,
                   c->d_tile_cnt, c->h_js.rec, c->h_js.partials, c->d_stage, c->d_state_p,
                   c->d_f2, c->h_js.partials_p, c->d_push, c->d_push_bdot, c->h_js.perm,
-                  c->h_js.sort_counts, c->h_js.bucket_base, c->h_js.gref};
+                  c->h_js.sort_counts, c->h_js.bucket_base, c->h_js.gref, c->h_js.partials_f};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);

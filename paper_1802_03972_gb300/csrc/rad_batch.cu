@@ -106,7 +106,7 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
     if (jobs[i]->tile.variant != variant) variant = kDefaultVariant;
 
   // Per-job chunking, capacities (may reallocate: drain this stream first).
-  struct Plan { int job; long long n; int ck, n_chunks; long long cost; JobStatic js; };
+  struct Plan { int job; long long n; int ck, n_chunks; TailPlan tail; long long cost; JobStatic js; };
   std::vector<Plan> plan;
   plan.reserve(n_jobs);
   bool drained = false;
@@ -118,24 +118,30 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
       fill_tiles(js, variant, default_omega_tile(variant, c->n_omega));
     const int ck = auto_chunk(c, variant, steps[i].n, js.n_tiles);
     const int nch = (int)((steps[i].n + ck - 1) / ck);
-    if (steps[i].n > c->h_js.n_cap || nch > c->h_js.chunk_cap) {
+    // chunked as the job alone would be (results equal bit for bit)
+    const TailPlan tail = tail_plan(variant_tensor_core(variant) && !js.literal, steps[i].n,
+                                    js.n_tiles, ck, nch, resident_ctas(variant));
+    const long long fine = tail.fine_floats(js.nt * js.wt);
+    if (steps[i].n > c->h_js.n_cap || nch > c->h_js.chunk_cap || fine > c->h_js.fine_cap) {
       if (!drained) {
         if (cudaStreamSynchronize(work) != cudaSuccess) return RAD_ECUDA;
         drained = true;
       }
-      rad_status s = ensure_capacity(c, steps[i].n, nch);
+      rad_status s = ensure_capacity(c, steps[i].n, nch, fine);
       if (s != RAD_OK) return s;
       if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RAD_ECUDA;
       js.rec = c->h_js.rec;
       js.n_cap = c->h_js.n_cap;
       js.partials = c->h_js.partials;
       js.chunk_cap = c->h_js.chunk_cap;
+      js.partials_f = c->h_js.partials_f;
+      js.fine_cap = c->h_js.fine_cap;
       js.perm = c->h_js.perm;
       js.sort_counts = c->h_js.sort_counts;
       js.bucket_base = c->h_js.bucket_base;
       js.gref = c->h_js.gref;
     }
-    plan.push_back({i, steps[i].n, ck, nch, (long long)js.n_tiles * nch * (long long)ck, js});
+    plan.push_back({i, steps[i].n, ck, nch, tail, (long long)js.n_tiles * nch * (long long)ck, js});
   }
   if (plan.empty()) return RAD_OK;
   // Largest jobs first, so the dynamic scheduler's tail holds small items.
@@ -189,10 +195,13 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
     K.dt = st.dt;
     K.ck = plan[p].ck;
     K.n_chunks = plan[p].n_chunks;
+    K.tail_tiles = plan[p].tail.tiles;
+    K.ck_f = plan[p].tail.ck;
+    K.n_chunks_f = plan[p].tail.n_chunks;
     K.item_begin = items;
     K.block_begin = blocks;
     K.sort_block_begin = sort_blocks;
-    items += (long long)plan[p].js.n_tiles * plan[p].n_chunks;
+    items += plan[p].tail.items(plan[p].js.n_tiles, plan[p].n_chunks);
     blocks += (int)((st.n + 255) / 256);
     sort_blocks += (int)((st.n + kSortBlock - 1) / kSortBlock);
   }

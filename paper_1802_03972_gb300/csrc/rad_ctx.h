@@ -77,7 +77,9 @@ void fill_tiles(JobStatic& js, int variant, int wt);
 int resident_ctas(int variant);
 int auto_chunk_for(int variant, long long n, int n_tiles);
 int auto_chunk(const rad_ctx* c, int variant, long long n, int n_tiles);
-rad_status ensure_capacity(rad_ctx* c, long long n, int n_chunks);
+// Capacity for n particles, n_chunks coarse chunks and fine_floats floats of
+// fine-tile partial sums (TailPlan::fine_floats).
+rad_status ensure_capacity(rad_ctx* c, long long n, int n_chunks, long long fine_floats = 0);
 rad_status enqueue_accumulate(rad_ctx* c, long long n, const double* r, const double* beta,
                               const double* bdot, const double* w, double t, double dt);
 rad_status upload_static(rad_ctx* c);

@@ -30,10 +30,14 @@ constexpr int kOmTab = 3;
 // shared-memory tiles (threads / directions-per-tile particles) for every
 // kernel variant and tile shape.
 constexpr int kChunkAlign = 256;
-// Automatic chunking aims at this many work items per resident block: enough
-// that the blocks finishing last wait on short items (measured on the LWFA
-// workload: 24 gave 7.13 ms per step, 16 gave 7.19) ...
-constexpr int kItemsPerCta = 24;
+// Automatic chunking aims at this many (coarse) work items per resident
+// block.  Each item has fixed costs (the first tile's exposed copy, zeroing and
+// writing its partial sums, ~5 us), so fewer, longer items are cheaper; the
+// end-of-launch tail they would leave is cut by the fine-chunked last tiles
+// (TailPlan).  Measured with the tensor-core variant 9 on the LWFA workload
+// (1e5 particles, 512 x 256 bins), kernel time: 8 items 6.897 ms, 6 and 10
+// 6.93-6.96, 16 6.927, 24 6.962, 4 7.03 (items of one size, 24: 7.08) ...
+constexpr int kItemsPerCta = 8;
 // ... but gives a work item at least this many particles, over which its fixed
 // costs (the first tile's exposed copy, zeroing and writing its partial sums)
 // spread: on the batched job mix of small jobs this measured 1 % faster.
@@ -77,7 +81,11 @@ struct JobStatic {
   const float* dir_tab;
   const double* dirs;
   float* state;
-  float* partials;
+  float* partials;                // [chunk_cap][kComps][n_bins]
+  // the fine-chunked last tiles of a call (see TailPlan):
+  // [n_chunks_f][kComps][tail_tiles][nt * wt], fine_cap floats
+  float* partials_f;
+  long long fine_cap;
   unsigned* tile_cnt;             // [n_tiles] arrival counters (self-resetting)
   float* rec;
   double* ref;                    // [4]: reference position xyz, t (per call)
@@ -113,7 +121,48 @@ struct JobCall {
   long long item_begin;  // first global work item of this job
   int block_begin;       // first pre-pass block of this job
   int sort_block_begin;  // first sort-histogram block of this job
+  // the job's last tail_tiles tiles take chunks of ck_f (n_chunks_f per tile)
+  int tail_tiles;
+  int ck_f;
+  int n_chunks_f;
+  int pad_;
 };
+
+// Finer work items for the last tiles of a job (tensor-core variants).  With
+// items of one size, the launch ends with the resident blocks finishing their
+// last items at spread-out times, about half an item idle per block.  A job
+// that fills the GPU at least twice over cuts its last L tiles into chunks of
+// a quarter of the size, L = ceil(grid / n_chunks) + 1: enough fine work for
+// every resident block to move on to it before the coarse items run out, so
+// the idle end is about half a fine item.  The plan depends on the job alone
+// (its size and tiling) and the device's resident blocks, so a job is
+// chunked alike alone, in a batch and in the server.
+struct TailPlan {
+  int tiles = 0;     // the job's last `tiles` tiles take the fine chunks
+  int ck = 0;        // their chunk, a multiple of kChunkAlign
+  int n_chunks = 0;  // their chunks per tile
+  long long items(int n_tiles, int n_chunks_coarse) const {
+    return (long long)(n_tiles - tiles) * n_chunks_coarse + (long long)tiles * n_chunks;
+  }
+  // floats of JobStatic::partials_f the plan needs
+  long long fine_floats(int bins_per_tile) const {
+    return (long long)n_chunks * kComps * tiles * bins_per_tile;
+  }
+};
+inline TailPlan tail_plan(bool tensor_core, long long n, int n_tiles, int ck, int n_chunks,
+                          long long grid) {
+  TailPlan t;
+  if (!tensor_core || n <= 0 || (long long)n_tiles * n_chunks < 2 * grid) return t;
+  int ckf = (ck / 4 + kChunkAlign - 1) / kChunkAlign * kChunkAlign;
+  if (ckf < kChunkAlign) ckf = kChunkAlign;
+  if (ckf >= ck) return t;
+  const long long L = (grid + n_chunks - 1) / n_chunks + 1;
+  if (2 * L > n_tiles) return t;
+  t.tiles = (int)L;
+  t.ck = ckf;
+  t.n_chunks = (int)((n + ckf - 1) / ckf);
+  return t;
+}
 
 struct LaunchArgs {
   const JobStatic* js;   // device [n_jobs]
@@ -145,10 +194,11 @@ struct Variant {
 // of 32 w passes);
 // 6: FP32-FMA with the paper's literal sum as well (literal contexts only);
 // 7: tensor-core accumulation in two frequency passes per staged particle tile;
-// 8: tensor-core accumulation, a warp covers 64 frequencies (w = 2), 2 CTAs/SM.
-constexpr int kNumVariants = 9;
+// 8: tensor-core accumulation, a warp covers 64 frequencies (w = 2), 2 CTAs/SM;
+// 9: as 8, with the phases' float-float cross terms formed by an MMA per block.
+constexpr int kNumVariants = 10;
 constexpr int kLiteralVariant = 6;
-constexpr int kDefaultVariant = 8;  // a new context's tile, and a mixed batch's
+constexpr int kDefaultVariant = 9;  // a new context's tile, and a mixed batch's
 inline Variant variant_info(int v) {
   switch (v) {
     case 1: return {256, 4, 1};
@@ -156,10 +206,13 @@ inline Variant variant_info(int v) {
     case 3:
     case 4: return {256, 1, 1};
     case 7: return {256, 1, 2};
-    case 8: return {256, 2, 1};
+    case 8:
+    case 9: return {256, 2, 1};
     default: return {256, 2, 1};
   }
 }
+// Tensor-core (mma.sync) accumulation variants.
+inline bool variant_tensor_core(int v) { return v == 3 || v == 4 || v == 7 || v == 8 || v == 9; }
 cudaError_t launch_readout_literal(const float* state_p, int n_bins, double* out, cudaStream_t s);
 
 // Launchers (rad_kernels.cu). All enqueue on `s` and return the launch error.

@@ -59,8 +59,10 @@ __device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
   const float d1 = fmaf(e10, ad0, fmaf(e11, ad1, e12 * ad2));
   const float d2 = fmaf(e20, ad0, fmaf(e21, ad1, e22 * ad2));
   const float dn = fmaf(nh0, ad0, fmaf(nh1, ad1, nh2 * ad2));
-  const float D = (g2 + fmaf(b1, b1, b2 * b2)) / (1.0f + bn);
-  const float iD = 1.0f / D;
+  // Approximate reciprocals (about 1 ulp): a relative error of a few 1e-7 in
+  // the amplitude, far below what the TF32 and MUFU steps leave.
+  const float D = (g2 + fmaf(b1, b1, b2 * b2)) * rcp_approx(1.0f + bn);
+  const float iD = rcp_approx(D);
   const float iD2 = iD * iD;
   const float a1 = -fmaf(b1, dn, d1 * D) * iD2;
   const float a2 = -fmaf(b2, dn, d2 * D) * iD2;
@@ -74,7 +76,9 @@ __device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
 // Shared memory: one raw particle tile (THREADS x 80 B, TMA destination) and
 // two record buffers.  FP32 variants: per record 3 float4 (values duplicated
 // for packed arithmetic); tensor-core variants: float2 dtau + 8 floats of
-// amplitude hi/lo parts.
+// amplitude hi/lo parts; with the cross terms on tensor cores (variant 9),
+// dtau hi + 8 floats of TF32 parts of dtau + 12 floats (8 used) of amplitude
+// hi/lo parts.
 // Tensor-core variants also keep their per-chunk (second-level) sums in
 // shared memory: 8 floats per thread and 16-frequency block of a warp (16 or
 // 32 per thread), one slot per thread and value.
@@ -91,6 +95,19 @@ __device__ __forceinline__ float2 phase2(float2 omh, float2 wh, float2 wl, float
   const float2 c1 = __fmul2_rn(wl, th);                            // cross terms, radians
   const float2 c2 = __ffma2_rn(wh, tl, c1);
   return __ffma2_rn(f0, k2Pi, c2);
+}
+
+// Phase of one frequency for a particle pair (packed over the particles): om2
+// holds omega/2pi (hi) in both halves, th2 the two particles' dtau hi parts, cr
+// their cross terms 2pi (omega_lo th + omega_hi tl) in radians, formed
+// elsewhere.  The turns om th are reduced exactly as in phase2.
+__device__ __forceinline__ float2 phase2x(float2 om2, float2 th2, float2 cr) {
+  const float2 kMag = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23
+  const float2 k2Pi = make_float2(6.28318530717958647692f, 6.28318530717958647692f);
+  const float2 t0 = __ffma2_rn(om2, th2, kMag);
+  const float2 q = __fadd2_rn(kMag, make_float2(-t0.x, -t0.y));
+  const float2 f0 = __ffma2_rn(om2, th2, q);
+  return __ffma2_rn(f0, k2Pi, cr);
 }
 
 // Phase in FP64 (wide path): omega/2pi times the float-float dtau plus an

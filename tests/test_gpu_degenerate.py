@@ -25,7 +25,7 @@ from paper_1802_03972_gb300 import build as _build  # noqa: E402
 _build.build()
 from paper_1802_03972_gb300 import rad  # noqa: E402
 
-VARIANTS = [0, 3, 7, 8]
+VARIANTS = [0, 3, 7, 8, 9]
 
 
 def run(omega, dirs, steps, variant, ff=(rad.FF_POINT, 0.0), scale_w=1.0, repeat=1):

@@ -66,7 +66,7 @@ def small_lwfa(n=2000, n_omega=100, n_side=8, seed=21):
     return wl
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 7, 8])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 7, 8, 9])
 def test_lwfa_small_full_grid_all_variants(variant):
     """LWFA-shaped bunch with weights, Gaussian form factor, ragged particle count
     (2000 = 31 x 64 + 16) and ragged frequency tile (100 of 128), 20 steps."""
@@ -87,16 +87,17 @@ def test_two_pass_variant_full_width_tile():
     check(ctx, ref)
 
 
-def test_wide_warp_variant_full_width_tile():
-    """Variant 8 gives each warp four 16-frequency blocks (64 frequencies): 300
-    frequencies give one 512-wide tile whose last warps are ragged or empty, over
-    9 directions and a ragged particle count; and 48 frequencies in a 64-wide
-    tile of 8 directions, the last tile holding one."""
+@pytest.mark.parametrize("variant", [8, 9])
+def test_wide_warp_variant_full_width_tile(variant):
+    """Variants 8 and 9 give each warp four 16-frequency blocks (64 frequencies):
+    300 frequencies give one 512-wide tile whose last warps are ragged or empty,
+    over 9 directions and a ragged particle count; and 48 frequencies in a
+    64-wide tile of 8 directions, the last tile holding one."""
     for n_omega, n_side, wt in ((300, 3, 512), (48, 3, 64)):
         wl = small_lwfa(n=1500, n_omega=n_omega, n_side=n_side, seed=23)
         ref = spectra_grid(oracle_run(wl, range(6)), wl)
-        ctx = gpu_run(wl, range(6), tile=(8, wt, 0))
-        assert ctx.get_tile()[:2] == (8, wt)
+        ctx = gpu_run(wl, range(6), tile=(variant, wt, 0))
+        assert ctx.get_tile()[:2] == (variant, wt)
         check(ctx, ref)
 
 
@@ -184,7 +185,7 @@ def test_edge_cases_small_sizes():
         check(ctx, ref)
 
 
-@pytest.mark.parametrize("variant", [3, 8])
+@pytest.mark.parametrize("variant", [3, 8, 9])
 def test_changing_particle_counts_between_calls(variant):
     """One context fed calls of 3000, 700, 3000, 257 and 1 particles with a fixed
     chunk of 512: the number of chunks, and so of partial-sum slots each tile's

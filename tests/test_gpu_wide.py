@@ -61,7 +61,7 @@ def run_pair(omega, dirs, data, ff=(oracle.FF_GAUSS, 0.1e-6), tile=None, flags=0
     return ctx, acc, shape
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 7, 8])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 7, 8, 9])
 def test_two_millimetre_bunch_all_variants(variant):
     """20000 particles over 2 mm at omega up to 1e20 rad/s: about 50 times the
     fast range about one reference, a few microns per sorted group."""
@@ -226,7 +226,7 @@ def test_wide_bunch_over_fifty_steps():
                 assert_parity(g, acc.spectra()[k].reshape(shape), what=f"{k} after {s + 1} steps")
 
 
-@pytest.mark.parametrize("variant", [0, 8])
+@pytest.mark.parametrize("variant", [0, 8, 9])
 def test_wide_call_tiles_on_the_fp64_path(variant):
     """A bunch 1 mm wide across the sort axis as well as along it, observed over
     +-0.3 rad: sorting along the mean direction cannot make the groups compact
