@@ -69,7 +69,9 @@ struct Smem {
   static constexpr size_t raw_bytes = (size_t)THREADS * kRecFields * sizeof(float);
   static constexpr size_t rec_bytes = (size_t)THREADS * (XT ? 84 : TC ? 40 : (LIT ? 64 : 48));
   static constexpr size_t l2_bytes = TC ? (size_t)THREADS * 16 * sizeof(float) * PASSES : 0;
-  static constexpr size_t bytes = raw_bytes + 2 * rec_bytes + l2_bytes;
+  // XT: the tile's direction rows (12 floats each; at most THREADS / 8 directions)
+  static constexpr size_t dir_bytes = XT ? (size_t)(THREADS / 8) * 12 * sizeof(float) : 0;
+  static constexpr size_t bytes = raw_bytes + 2 * rec_bytes + l2_bytes + dir_bytes;
 };
 
 struct TileGeom {
@@ -676,6 +678,16 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
   const long long k_end = min(k_begin + (long long)item.ck, K.n);
   const int n_kt = (int)((k_end - k_begin + g.KT - 1) / g.KT);
   if (threadIdx.x == 0) issue_tile(J, k_begin, g.KT, raw, bar);
+  // XT: the tile's direction rows, staged once per item for stage 1 (the
+  // previous item's last reads of them precede its closing barriers).
+  float* sdir = reinterpret_cast<float*>(smem + S::raw_bytes + 2 * S::rec_bytes + S::l2_bytes);
+  if constexpr (XT) {
+    for (int t = threadIdx.x; t < 12 * g.NT; t += THREADS) {
+      const int dl = t / 12, k = t - dl * 12;
+      sdir[t] = __ldg(J.dir_tab + (size_t)k * J.n_dir + min(g.d0 + dl, J.n_dir - 1));
+    }
+    __syncthreads();
+  }
   for (int it = 0; it < n_kt; ++it) {
     const long long kt = k_begin + (long long)it * g.KT;
     const int kn = (int)min((long long)g.KT, k_end - kt);
@@ -695,9 +707,14 @@ __device__ __forceinline__ bool process_item_tc(const JobStatic& J, const JobCal
     bool slow = false;
     if (landed) {
       float th = 0.f, tl = 0.f, a[4] = {0.f, 0.f, 0.f, 0.f};
-      if (s1_kk < kn)
-        slow = !compute_record(raw + s1_kk * kRecFields, J.dir_tab, J.n_dir, s1_d, J.tau_fast, th,
-                               tl, a);
+      if (s1_kk < kn) {
+        if constexpr (XT)
+          slow = !compute_record(raw + s1_kk * kRecFields, dir_row_staged(sdir + 12 * s1_dl),
+                                 J.tau_fast, th, tl, a);
+        else
+          slow = !compute_record(raw + s1_kk * kRecFields, J.dir_tab, J.n_dir, s1_d, J.tau_fast,
+                                 th, tl, a);
+      }
       // Particles past kn are zero padding of the last 8-particle MMA step.
       const int slot = s1_dl * g.KT + s1_kk;
       const uint32_t h0 = tf32_hi(a[0]), h1 = tf32_hi(a[1]), h2 = tf32_hi(a[2]), h3 = tf32_hi(a[3]);

@@ -12,10 +12,33 @@
 namespace radimpl {
 namespace dev {
 
+// One direction's row of the direction table: n (hi, lo) and the transverse
+// basis e1, e2.
+struct DirRow {
+  float nh0, nh1, nh2, nl0, nl1, nl2, e10, e11, e12, e20, e21, e22;
+};
+
+// Row d of the direction table dt_ ([12][n_dir] floats, global memory).
+__device__ __forceinline__ DirRow dir_row(const float* __restrict__ dt_, int n_dir, int d) {
+  DirRow r;
+  r.nh0 = __ldg(dt_ + 0 * n_dir + d), r.nh1 = __ldg(dt_ + 1 * n_dir + d), r.nh2 = __ldg(dt_ + 2 * n_dir + d);
+  r.nl0 = __ldg(dt_ + 3 * n_dir + d), r.nl1 = __ldg(dt_ + 4 * n_dir + d), r.nl2 = __ldg(dt_ + 5 * n_dir + d);
+  r.e10 = __ldg(dt_ + 6 * n_dir + d), r.e11 = __ldg(dt_ + 7 * n_dir + d), r.e12 = __ldg(dt_ + 8 * n_dir + d);
+  r.e20 = __ldg(dt_ + 9 * n_dir + d), r.e21 = __ldg(dt_ + 10 * n_dir + d), r.e22 = __ldg(dt_ + 11 * n_dir + d);
+  return r;
+}
+
+// The same row staged in shared memory as 12 consecutive floats (16-byte aligned).
+__device__ __forceinline__ DirRow dir_row_staged(const float* s) {
+  const float4 a = reinterpret_cast<const float4*>(s)[0];
+  const float4 b = reinterpret_cast<const float4*>(s)[1];
+  const float4 c = reinterpret_cast<const float4*>(s)[2];
+  return DirRow{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+}
+
 // Stage 1: record of (particle, direction).  raw: the particle's 80-byte record.
 // Returns false when |dtau| is beyond the fast phase path's range.
-__device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
-                                               const float* __restrict__ dt_, int n_dir, int d,
+__device__ __forceinline__ bool compute_record(const float* __restrict__ raw, const DirRow& dr,
                                                float tau_fast, float& th, float& tl, float amp[4]) {
   const float4 q0 = *reinterpret_cast<const float4*>(raw);
   const float4 q1 = *reinterpret_cast<const float4*>(raw + 4);
@@ -25,10 +48,8 @@ __device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
   const float sh0 = q0.x, sh1 = q0.y, sh2 = q0.z, sl0 = q0.w, sl1 = q1.x, sl2 = q1.y;
   const float bh0 = q1.z, bh1 = q1.w, bh2 = q2.x, bl0 = q2.y, bl1 = q2.z, bl2 = q2.w;
   const float ad0 = q3.x, ad1 = q3.y, ad2 = q3.z, g2 = q3.w, ww = q4.x, sw = q4.y;
-  const float nh0 = __ldg(dt_ + 0 * n_dir + d), nh1 = __ldg(dt_ + 1 * n_dir + d), nh2 = __ldg(dt_ + 2 * n_dir + d);
-  const float nl0 = __ldg(dt_ + 3 * n_dir + d), nl1 = __ldg(dt_ + 4 * n_dir + d), nl2 = __ldg(dt_ + 5 * n_dir + d);
-  const float e10 = __ldg(dt_ + 6 * n_dir + d), e11 = __ldg(dt_ + 7 * n_dir + d), e12 = __ldg(dt_ + 8 * n_dir + d);
-  const float e20 = __ldg(dt_ + 9 * n_dir + d), e21 = __ldg(dt_ + 10 * n_dir + d), e22 = __ldg(dt_ + 11 * n_dir + d);
+  const float nh0 = dr.nh0, nh1 = dr.nh1, nh2 = dr.nh2, nl0 = dr.nl0, nl1 = dr.nl1, nl2 = dr.nl2;
+  const float e10 = dr.e10, e11 = dr.e11, e12 = dr.e12, e20 = dr.e20, e21 = dr.e21, e22 = dr.e22;
 
   // n . s in float-float: exact products (TwoProduct via fma) and exact sums
   // (Knuth TwoSum) of the hi parts, all first-order lo terms added in FP32.
@@ -71,6 +92,12 @@ __device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
   amp[2] = sw * a1;  // V . e1
   amp[3] = sw * a2;  // V . e2
   return fabsf(th) <= tau_fast;  // false for NaN as well
+}
+
+__device__ __forceinline__ bool compute_record(const float* __restrict__ raw,
+                                               const float* __restrict__ dt_, int n_dir, int d,
+                                               float tau_fast, float& th, float& tl, float amp[4]) {
+  return compute_record(raw, dir_row(dt_, n_dir, d), tau_fast, th, tl, amp);
 }
 
 // Shared memory: one raw particle tile (THREADS x 80 B, TMA destination) and
