@@ -999,6 +999,10 @@ def main():
         peaks["tensor"] = {"mma_sync_tf32_mac_per_clk_sm": q[0],
                            "tcgen05_tf32_clk_per_mma_n16_64_128_256": list(q[1:5]),
                            "tcgen05_f16_clk_per_mma_n16_256": list(q[5:7]), "probe_mhz": q[7]}
+        lp = rad.probe_loop()
+        peaks["update_loop_mufu_per_clk_sm"] = {
+            "variant8": lp[0], "no_split": lp[2], "no_mma": lp[4], "neither": lp[6], "variant9": lp[8],
+            "probe_mhz": [lp[i] for i in range(1, 10, 2)]}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -32,6 +32,22 @@ int rad_probe_peaks(double* out, int n_out);
  * error code.  Allocates a few MB of device memory for the duration of the call. */
 int rad_probe_tensor(double* out, int n_out);
 
+/* rad_probe_loop - the accumulate kernel's update loop with parts removed, on
+ * the current device (timing only: the arithmetic is real, the results are
+ * discarded).  One 256-particle tile of synthetic records in shared memory is
+ * swept by 256-thread blocks, 2 per SM, each warp holding four 16-frequency
+ * MMA blocks, with no stage 1, barrier or epilogue.  Per mode m, out[2 m] =
+ * MUFU sin/cos lane-operations per SM clock and out[2 m + 1] = the effective
+ * clock (MHz):
+ *   m = 0  the variant-8 update: phase reduction, TF32 hi/lo split, 4 mma.sync;
+ *   m = 1  without the split (the raw sin/cos bits into the same 4 MMAs);
+ *   m = 2  the split without the MMAs (its results folded by XOR);
+ *   m = 3  neither (sin/cos consumed by 2 packed FMAs);
+ *   m = 4  the variant-9 update (phase cross terms by one more mma.sync).
+ * out: host array of n_out >= 10 doubles.  Returns 0, or a CUDA error code.
+ * Allocates a few MB of device memory for the duration of the call. */
+int rad_probe_loop(double* out, int n_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rad_stage.cuh"
+
 namespace {
 
 constexpr int kThreads = 512;
@@ -282,6 +284,134 @@ __global__ void __launch_bounds__(32, 1) k_umma(int n_mma, long long* cyc, int* 
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tb) : "memory");
 }
 
+// ---- the accumulate kernel's update loop with parts removed (timing only) ----
+// One 256-particle tile of synthetic records in shared memory, swept `reps`
+// times by 256 threads (2 blocks per SM, as the tensor-core kernels run), each
+// warp holding four 16-frequency MMA blocks, the particle loop unrolled 8x, no
+// barriers, no stage 1 and no epilogue.  MODE:
+//   0  the variant-8 block: two packed phase reductions, the TF32 hi/lo split
+//      and four mma.sync per 16-frequency x 8-particle block;
+//   1  no split: the raw sin/cos bits go into the same four MMAs;
+//   2  the split, no MMA: its outputs are folded by XOR (three-input LOP3s);
+//   3  neither: sin/cos consumed by two packed FMAs;
+//   4  the variant-9 block: the phase cross terms by one more mma.sync.
+// The results are meaningless; only the pipes' throughput is of interest.
+constexpr int kLoopNB = 4, kLoopKT = 256;
+
+template <int MODE>
+__device__ __forceinline__ void loop_block(float2 pA, float2 pB, uint32_t b0, uint32_t b1,
+                                           float dre[4], float dim[4], uint32_t& xacc) {
+  using namespace radimpl::dev;
+  if constexpr (MODE == 0 || MODE == 4) {
+    tc_block(pA, pB, b0, b1, dre, dim);
+    return;
+  }
+  const float2 cA = make_float2(cos_approx(pA.x), cos_approx(pA.y));
+  const float2 sA = make_float2(sin_approx(pA.x), sin_approx(pA.y));
+  const float2 cB = make_float2(cos_approx(pB.x), cos_approx(pB.y));
+  const float2 sB = make_float2(sin_approx(pB.x), sin_approx(pB.y));
+  if constexpr (MODE == 1) {
+    mma_tf32(dre, __float_as_uint(cA.x), __float_as_uint(cA.y), __float_as_uint(cB.x), __float_as_uint(cB.y), b0, b1);
+    mma_tf32(dre, __float_as_uint(cA.y), __float_as_uint(cA.x), __float_as_uint(cB.y), __float_as_uint(cB.x), b0, b1);
+    mma_tf32(dim, __float_as_uint(sA.x), __float_as_uint(sA.y), __float_as_uint(sB.x), __float_as_uint(sB.y), b0, b1);
+    mma_tf32(dim, __float_as_uint(sA.y), __float_as_uint(sA.x), __float_as_uint(sB.y), __float_as_uint(sB.x), b0, b1);
+  } else if constexpr (MODE == 3) {
+    const float2 bb = make_float2(__uint_as_float(b0), __uint_as_float(b1));
+    float2* r = reinterpret_cast<float2*>(dre);
+    float2* i = reinterpret_cast<float2*>(dim);
+    r[0] = __ffma2_rn(cA, bb, r[0]);
+    r[1] = __ffma2_rn(cB, bb, r[1]);
+    i[0] = __ffma2_rn(sA, bb, i[0]);
+    i[1] = __ffma2_rn(sB, bb, i[1]);
+  } else {
+    uint32_t h[8];
+    float2 lo[4];
+    split_pair(cA, h[0], h[1], lo[0]);
+    split_pair(cB, h[2], h[3], lo[1]);
+    split_pair(sA, h[4], h[5], lo[2]);
+    split_pair(sB, h[6], h[7], lo[3]);
+    uint32_t x = xacc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(x) : "r"(x), "r"(h[2 * k]), "r"(h[2 * k + 1]));
+      asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(x) : "r"(x), "r"(__float_as_uint(lo[k].x)), "r"(__float_as_uint(lo[k].y)));
+    }
+    xacc = x;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 2) k_loop(float* out, long long* cyc, int reps) {
+  using namespace radimpl::dev;
+  __shared__ float2 tw[kLoopKT];
+  __shared__ float aw[kLoopKT * 8];
+  const int t = threadIdx.x;
+  tw[t] = make_float2(6.0e-14f * (float)((t * 37) % 256 - 128) / 128.0f, 1.0e-21f * (float)(t % 7 - 3));
+  for (int j = 0; j < 8; ++j) aw[t * 8 + j] = 1.0f + 0.01f * (float)((t + j) % 13);
+  __syncthreads();
+  const int warp = t >> 5, lane = t & 31, r = lane >> 2, c = lane & 3;
+  float2 omh[kLoopNB], wh[kLoopNB], wl[kLoopNB], omr[kLoopNB], omr8[kLoopNB];
+  uint32_t xa[kLoopNB][4];
+  float dre[kLoopNB][4], dim[kLoopNB][4];
+  for (int b = 0; b < kLoopNB; ++b) {
+    const float f0 = 1.6e13f * __powf(1.0276f, (float)(warp * 64 + 16 * b + r)), f1 = f0 * 1.2456f;
+    omh[b] = make_float2(f0, f1);
+    wh[b] = make_float2(6.2831855f * f0, 6.2831855f * f1);
+    wl[b] = make_float2(1e-7f * f0, 1e-7f * f1);
+    omr[b] = make_float2(f0, f0);
+    omr8[b] = make_float2(f1, f1);
+    for (int i = 0; i < 4; ++i) xa[b][i] = tf32_hi(wl[b].x * (float)(1 + i));
+    for (int e = 0; e < 4; ++e) dre[b][e] = dim[b][e] = 0.0f;
+  }
+  uint32_t xacc = 0;
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int rep = 0; rep < reps; ++rep) {
+#pragma unroll 8
+    for (int kk = 0; kk < kLoopKT; kk += 8) {
+      if constexpr (MODE == 4) {
+        const float2 th2 = make_float2(tw[kk + 2 * c].x, tw[kk + 2 * c + 1].x);
+        const uint32_t r0 = tf32_hi(aw[(kk + r) * 8 + 2 * c]), r1 = tf32_hi(aw[(kk + r) * 8 + 2 * c + 1]);
+        const uint32_t b0 = __float_as_uint(aw[(kk + 2 * c) * 8 + r]);
+        const uint32_t b1 = __float_as_uint(aw[(kk + 2 * c + 1) * 8 + r]);
+#pragma unroll
+        for (int b = 0; b < kLoopNB; ++b) {
+          float cr[4];
+          mma_tf32_zero(cr, xa[b][0], xa[b][1], xa[b][2], xa[b][3], r0, r1);
+          const float2 p0 = phase2x(omr[b], th2, make_float2(cr[0], cr[1]));
+          const float2 p8 = phase2x(omr8[b], th2, make_float2(cr[2], cr[3]));
+          loop_block<MODE>(make_float2(p0.x, p8.x), make_float2(p0.y, p8.y), b0, b1, dre[b], dim[b], xacc);
+        }
+      } else {
+        const float2 tA = tw[kk + c], tB = tw[kk + c + 4];
+        const uint32_t b0 = __float_as_uint(aw[(kk + c) * 8 + r]);
+        const uint32_t b1 = __float_as_uint(aw[(kk + c + 4) * 8 + r]);
+        const float2 thA = make_float2(tA.x, tA.x), tlA = make_float2(tA.y, tA.y);
+        const float2 thB = make_float2(tB.x, tB.x), tlB = make_float2(tB.y, tB.y);
+#pragma unroll
+        for (int b = 0; b < kLoopNB; ++b) {
+          const float2 pA = phase2(omh[b], wh[b], wl[b], thA, tlA);
+          const float2 pB = phase2(omh[b], wh[b], wl[b], thB, tlB);
+          loop_block<MODE>(pA, pB, b0, b1, dre[b], dim[b], xacc);
+        }
+      }
+    }
+  }
+  const long long t1 = clock64();
+  float sum = (float)xacc;
+  for (int b = 0; b < kLoopNB; ++b)
+    for (int e = 0; e < 4; ++e) sum += dre[b][e] + dim[b][e];
+  out[blockIdx.x * blockDim.x + t] = sum;
+  __syncthreads();
+  if (t == 0) {
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    cyc[3 * blockIdx.x] = t0;
+    cyc[3 * blockIdx.x + 1] = t1;
+    cyc[3 * blockIdx.x + 2] = (long long)sm;
+  }
+}
+
 // Operations per SM clock and the effective clock (MHz) of a probe launch of
 // nb blocks, each doing ops_per_block operations: every SM is timed from its
 // first block's start to its last block's end, so blocks that an SM ran one
@@ -450,6 +580,52 @@ int rad_probe_tensor(double* out, int n_out) {
   cudaFree(d_out);
   cudaFree(d_cyc);
   cudaFree(d_err);
+  return (int)e;
+}
+
+// The update loop with parts removed (k_loop): out[2 m], out[2 m + 1] = MUFU
+// lane-ops per SM clock and the effective clock (MHz) of mode m = 0..4.
+int rad_probe_loop(double* out, int n_out) {
+  if (out == nullptr || n_out < 10) return (int)cudaErrorInvalidValue;
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = n_sm * 2;
+  float* d_out = nullptr;
+  long long* d_cyc = nullptr;
+  cudaError_t e = cudaMalloc(&d_out, sizeof(float) * blocks * 256);
+  if (e == cudaSuccess) e = cudaMalloc(&d_cyc, sizeof(long long) * 3 * blocks);
+  long long* h_cyc = new long long[3 * blocks];
+  const int sm_ids = 2 * n_sm + 64;
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  const int reps = 200;
+  // MUFU lane-ops per block: 256 threads x reps x 32 steps x 4 MMA blocks x 8
+  const double ops = 256.0 * reps * (kLoopKT / 8) * kLoopNB * 8;
+  auto run = [&](auto kern, double* res) {
+    if (e != cudaSuccess) return;
+    kern<<<blocks, 256>>>(d_out, d_cyc, 2);
+    cudaEventRecord(ev0);
+    kern<<<blocks, 256>>>(d_out, d_cyc, reps);
+    cudaEventRecord(ev1);
+    e = cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    if (e == cudaSuccess) e = cudaMemcpy(h_cyc, d_cyc, sizeof(long long) * 3 * blocks, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) rate_per_sm(h_cyc, blocks, ops, ms, sm_ids, &res[0], &res[1]);
+  };
+  run(k_loop<0>, out + 0);
+  run(k_loop<1>, out + 2);
+  run(k_loop<2>, out + 4);
+  run(k_loop<3>, out + 6);
+  run(k_loop<4>, out + 8);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  delete[] h_cyc;
+  cudaFree(d_out);
+  cudaFree(d_cyc);
   return (int)e;
 }
 

@@ -62,7 +62,6 @@ namespace {
 
 using namespace dev;
 
-constexpr uint32_t kTf32Mask = 0xFFFFE000u;  // sign, exponent, 10 mantissa bits
 
 template <int THREADS, bool TC, bool LIT = false, int PASSES = 1, bool XT = false>
 struct Smem {
@@ -532,70 +531,6 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
 }
 
 // ------------------------------------------------------ tensor-core variant
-__device__ __forceinline__ void mma_tf32(float d[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ uint32_t tf32_hi(float x) { return __float_as_uint(x) & kTf32Mask; }
-
-// Splits a packed pair into TF32 hi bits and the exact FP32 rest.
-__device__ __forceinline__ void split_pair(float2 v, uint32_t& h0, uint32_t& h1, float2& lo) {
-  h0 = tf32_hi(v.x);
-  h1 = tf32_hi(v.y);
-  lo = __fadd2_rn(v, make_float2(-__uint_as_float(h0), -__uint_as_float(h1)));
-}
-
-// The TF32 value nearest to x (ties away from zero), as bits.
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t y;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-  return y;
-}
-
-// x ~ hi + lo, both TF32 values, |x - hi - lo| <= 2^-22 |x|.
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32_rna(x);
-  lo = tf32_rna(__fsub_rn(x, __uint_as_float(hi)));
-}
-
-// d = A B (m16n8k8 TF32, zero accumulator).
-__device__ __forceinline__ void mma_tf32_zero(float d[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                              uint32_t a3, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%10,%10,%10,%10};"
-      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(0.0f));
-}
-
-// One 16-frequency x 8-particle MMA block: pA / pB are the phases of the
-// frequency rows (r, r+8) for particles (c, c+4) of the fragment layout.
-__device__ __forceinline__ void tc_block(float2 pA, float2 pB, uint32_t b0, uint32_t b1,
-                                         float dre[4], float dim[4]) {
-  const float2 cA = make_float2(cos_approx(pA.x), cos_approx(pA.y));
-  const float2 sA = make_float2(sin_approx(pA.x), sin_approx(pA.y));
-  const float2 cB = make_float2(cos_approx(pB.x), cos_approx(pB.y));
-  const float2 sB = make_float2(sin_approx(pB.x), sin_approx(pB.y));
-  uint32_t ca0, ca1, cb0, cb1, sa0, sa1, sb0, sb1;
-  float2 caL, cbL, saL, sbL;
-  split_pair(cA, ca0, ca1, caL);
-  split_pair(cB, cb0, cb1, cbL);
-  split_pair(sA, sa0, sa1, saL);
-  split_pair(sB, sb0, sb1, sbL);
-  // A fragment (m16n8k8 tf32): a0 = (row r, k c), a1 = (r+8, c), a2 = (r, c+4), a3 = (r+8, c+4)
-  mma_tf32(dre, ca0, ca1, cb0, cb1, b0, b1);
-  mma_tf32(dre, __float_as_uint(caL.x), __float_as_uint(caL.y), __float_as_uint(cbL.x),
-           __float_as_uint(cbL.y), b0, b1);
-  mma_tf32(dim, sa0, sa1, sb0, sb1, b0, b1);
-  mma_tf32(dim, __float_as_uint(saL.x), __float_as_uint(saL.y), __float_as_uint(sbL.x),
-           __float_as_uint(sbL.y), b0, b1);
-}
-
 // Warp layout: warp w handles direction d0 + w / (WT/(16 NB)) and 16 NB
 // frequencies (NB 16-row MMA blocks) starting at o0 + 16 NB (w % (WT/(16 NB))).
 // XT: the phases' cross terms 2pi (omega_lo th + omega_hi tl) come from one

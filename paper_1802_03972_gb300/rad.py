@@ -34,7 +34,7 @@ EXPORTS = [
     "rad_batch_sync", "rad_batch_destroy", "rad_server_create", "rad_server_set_policy", "rad_job_submit", "rad_job_feed",
     "rad_job_finish", "rad_job_poll", "rad_job_result", "rad_server_stats_get",
     "rad_server_destroy", "rad_status_str", "rad_last_error", "rad_kernel_launch_count",
-    "rad_probe_peaks", "rad_probe_tensor", "rad_profile_enable", "rad_profile_read", "rad_profile_clock", "rad_accumulate_static",
+    "rad_probe_peaks", "rad_probe_tensor", "rad_probe_loop", "rad_profile_enable", "rad_profile_read", "rad_profile_clock", "rad_accumulate_static",
     "rad_static_status",
     "rad_spectrum_literal", "rad_push_step", "rad_push_flush",
     "rad_selftest_wait", "rad_selftest_stage1", "rad_selftest_phase",
@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH):
         "rad_kernel_launch_count": (i64, []),
         "rad_probe_peaks": (ctypes.c_int, [vp, ctypes.c_int]),
         "rad_probe_tensor": (ctypes.c_int, [vp, ctypes.c_int]),
+        "rad_probe_loop": (ctypes.c_int, [vp, ctypes.c_int]),
         "rad_profile_enable": (st, [vp, i32]),
         "rad_profile_read": (st, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(i64)]),
         "rad_profile_clock": (st, [vp, ctypes.POINTER(dbl)]),
@@ -235,6 +236,17 @@ def probe_tensor() -> np.ndarray:
     rc = load().rad_probe_tensor(out.ctypes.data, 8)
     if rc != 0:
         raise RuntimeError(f"rad_probe_tensor failed with CUDA error {rc}")
+    return out
+
+
+def probe_loop() -> np.ndarray:
+    """rad_probe_loop: [MUFU lane-ops/clk/SM, MHz] for the update loop as it is (0),
+    without the TF32 split (1), without the MMAs (2), without either (3), and the
+    variant-9 loop (4)."""
+    out = np.zeros(10)
+    rc = load().rad_probe_loop(out.ctypes.data, 10)
+    if rc != 0:
+        raise RuntimeError(f"rad_probe_loop failed with CUDA error {rc}")
     return out
 
 

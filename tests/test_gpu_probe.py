@@ -1,4 +1,4 @@
-"""Pipe-throughput probes (rad_probe_peaks, rad_probe_tensor): the rates they
+"""Pipe-throughput probes (rad_probe_peaks, rad_probe_tensor, rad_probe_loop): the rates they
 report are per SM clock, so they must lie at or below the nominal per-SM widths
 of the units (FP32 FMA 128 lanes, MUFU 16; legacy mma.sync TF32 about 500 multiply-adds) and
 near them, and the effective clock must be a real SM clock."""
@@ -36,3 +36,17 @@ def test_tensor_probe():
     assert tf32[3] >= 128 * 256 * 8 / 2100.0       # at most ~2048 TF32 MACs per clock per SM
     assert all(c > 0 for c in q[5:7])
     assert 500.0 <= q[7] <= 2200.0, q[7]
+
+
+def test_update_loop_probe():
+    """The update loop's MUFU rate lies under the unit's 16 per SM clock in every
+    mode, and taking work out of the loop (the split, the MMAs, both) never
+    slows it: the decomposition behind the kernel's roofline fraction."""
+    lp = rad.probe_loop()
+    full8, no_split, no_mma, neither, full9 = lp[0], lp[2], lp[4], lp[6], lp[8]
+    for rate in (full8, no_split, no_mma, neither, full9):
+        assert 8.0 <= rate <= 16.0 * 1.02, lp
+    assert neither >= max(no_split, no_mma) * 0.98, lp
+    assert min(no_split, no_mma) >= full8 * 0.98, lp
+    for mhz in lp[1:10:2]:
+        assert 500.0 <= mhz <= 2200.0, mhz
