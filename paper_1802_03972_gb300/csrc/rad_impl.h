@@ -35,8 +35,8 @@ constexpr int kChunkAlign = 256;
 // writing its partial sums, ~5 us), so fewer, longer items are cheaper; the
 // end-of-launch tail they would leave is cut by the fine-chunked last tiles
 // (TailPlan).  Measured with the tensor-core variant 9 on the LWFA workload
-// (1e5 particles, 512 x 256 bins), kernel time: 8 items 6.897 ms, 6 and 10
-// 6.93-6.96, 16 6.927, 24 6.962, 4 7.03 (items of one size, 24: 7.08) ...
+// (1e5 particles, 512 x 256 bins), kernel time per step: 8 items 6.858 ms, 6
+// 6.916, 10 6.882, 16 6.880, 24 6.915, 4 6.984 (items of one size, 24: 6.957) ...
 constexpr int kItemsPerCta = 8;
 // ... but gives a work item at least this many particles, over which its fixed
 // costs (the first tile's exposed copy, zeroing and writing its partial sums)
