@@ -146,11 +146,14 @@ int resident_ctas(int variant) {
   return device_sm_count() * accumulate_blocks_per_sm(variant);
 }
 
-// Particles per work item: about 16 items per resident CTA in total, items a
-// multiple of the shared-memory tile.  Depends only on the job's shape, n and
-// the device, so a job is chunked the same way alone and in a batch.
-int auto_chunk_for(int variant, long long n, int n_tiles) {
-  const long long target = (long long)kItemsPerCta * resident_ctas(variant);
+// Particles per (coarse) work item: kItemsPerCta items per resident CTA in
+// total when the job's last tiles are fine-chunked (fine_tail), else
+// kItemsPerCtaUniform; items a multiple of the shared-memory tile.  Depends only
+// on the job's shape, n and the device, so a job is chunked the same way alone
+// and in a batch.
+int auto_chunk_for(int variant, long long n, int n_tiles, bool fine_tail) {
+  const long long target =
+      (long long)(fine_tail ? kItemsPerCta : kItemsPerCtaUniform) * resident_ctas(variant);
   long long chunks = (target + n_tiles - 1) / n_tiles;
   const long long max_chunks = (n + kChunkAlign - 1) / kChunkAlign;
   chunks = std::max(1LL, std::min(chunks, max_chunks));
@@ -163,7 +166,7 @@ int auto_chunk_for(int variant, long long n, int n_tiles) {
 
 int auto_chunk(const rad_ctx* c, int variant, long long n, int n_tiles) {
   if (c->tile.chunk > 0) return c->tile.chunk;
-  return auto_chunk_for(variant, n, n_tiles);
+  return auto_chunk_for(variant, n, n_tiles, variant_tensor_core(variant) && !c->h_js.literal);
 }
 
 rad_status upload_static(rad_ctx* c) {

@@ -75,7 +75,8 @@ int default_omega_tile(int variant, int n_omega);
 bool valid_omega_tile(int variant, int wt);
 void fill_tiles(JobStatic& js, int variant, int wt);
 int resident_ctas(int variant);
-int auto_chunk_for(int variant, long long n, int n_tiles);
+// fine_tail: the job's last tiles are fine-chunked (TailPlan), which allows longer items.
+int auto_chunk_for(int variant, long long n, int n_tiles, bool fine_tail);
 int auto_chunk(const rad_ctx* c, int variant, long long n, int n_tiles);
 // Capacity for n particles, n_chunks coarse chunks and fine_floats floats of
 // fine-tile partial sums (TailPlan::fine_floats).

@@ -31,13 +31,19 @@ constexpr int kOmTab = 3;
 // kernel variant and tile shape.
 constexpr int kChunkAlign = 256;
 // Automatic chunking aims at this many (coarse) work items per resident
-// block.  Each item has fixed costs (the first tile's exposed copy, zeroing and
-// writing its partial sums, ~5 us), so fewer, longer items are cheaper; the
-// end-of-launch tail they would leave is cut by the fine-chunked last tiles
-// (TailPlan).  Measured with the tensor-core variant 9 on the LWFA workload
+// block when the job's last tiles are fine-chunked (TailPlan: tensor-core
+// variants, not literal).  Each item has fixed costs (the first tile's exposed
+// copy, zeroing and writing its partial sums, ~5 us), so fewer, longer items
+// are cheaper; the end-of-launch tail they would leave is cut by the fine-
+// chunked last tiles.  Measured with the tensor-core variant 9 on the LWFA workload
 // (1e5 particles, 512 x 256 bins), kernel time per step: 8 items 6.858 ms, 6
 // 6.916, 10 6.882, 16 6.880, 24 6.915, 4 6.984 (items of one size, 24: 6.957) ...
 constexpr int kItemsPerCta = 8;
+// ... and this many without the fine-chunked tail (FP32 variants, the literal
+// sum, the allocation-free entry): there the blocks that finish last wait on at
+// most one item, so shorter items shorten the tail (variant 8 before the fine
+// tail: 24 items 7.13 ms per step, 16 items 7.19) ...
+constexpr int kItemsPerCtaUniform = 24;
 // ... but gives a work item at least this many particles, over which its fixed
 // costs (the first tile's exposed copy, zeroing and writing its partial sums)
 // spread: on the batched job mix of small jobs this measured 1 % faster.

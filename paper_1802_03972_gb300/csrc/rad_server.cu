@@ -73,15 +73,15 @@ struct Job {
 
 size_t estimate_footprint(const rad_job_desc& d) {
   const size_t nb = (size_t)d.n_omega * d.n_dir;
-  // Per-chunk partial sums (32 B per bin and chunk).  The server's contexts run
-  // the default variant with automatic chunking, which aims at kItemsPerCta work
-  // items per resident block; with B bins per tile, chunks x bins <=
-  // kItemsPerCta x resident blocks x B + bins.  There are also never more
-  // chunks than 256-particle groups.
+  // Per-chunk partial sums (32 B per bin and chunk).  Automatic chunking aims
+  // at kItemsPerCta work items per resident block with the fine-chunked tail
+  // and kItemsPerCtaUniform (the larger) without it; with B bins per tile,
+  // chunks x bins <= kItemsPerCtaUniform x resident blocks x B + bins.  There
+  // are also never more chunks than 256-particle groups.
   const Variant v = variant_info(kDefaultVariant);
   const size_t bins_per_tile = (size_t)v.threads * v.w * v.passes;
   const size_t by_particles = nb * (size_t)((d.max_particles + kChunkAlign - 1) / kChunkAlign);
-  const size_t by_items = (size_t)kItemsPerCta * resident_ctas(kDefaultVariant) * bins_per_tile + nb;
+  const size_t by_items = (size_t)kItemsPerCtaUniform * resident_ctas(kDefaultVariant) * bins_per_tile + nb;
   const size_t partials = 32 * std::min(by_particles, by_items);
   // The fine-chunked last tiles' partial sums (TailPlan): with L tiles of
   // n_f = 4 n_c + 1 chunks, L = grid / n_c + 2 at most, L n_f <= 5 grid + 8 n_c + 2;

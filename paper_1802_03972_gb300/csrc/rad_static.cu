@@ -173,7 +173,7 @@ extern "C" rad_status rad_accumulate_static(const double* omega, int32_t n_omega
   js.n_bins = n_omega * n_dir;
   fill_tiles(js, variant, default_omega_tile(variant, n_omega));
   if (js.n_tiles > kMaxTiles) return RAD_EINVAL;
-  int ck = auto_chunk_for(variant, n, js.n_tiles);
+  int ck = auto_chunk_for(variant, n, js.n_tiles, false);  // (no fine-chunked tail here)
   int n_chunks = (int)((n + ck - 1) / ck);
   if (n_chunks > kMaxChunks) {
     long long c2 = (n + kMaxChunks - 1) / kMaxChunks;

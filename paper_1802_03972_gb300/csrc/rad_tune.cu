@@ -149,7 +149,8 @@ extern "C" rad_status rad_tune(rad_ctx* c, int64_t n) {
       if (ckm) {
         JobStatic js = c->h_js;
         fill_tiles(js, t.variant, t.omega_tile);
-        const int ck = auto_chunk_for(t.variant, nt, js.n_tiles);
+        const int ck = auto_chunk_for(t.variant, nt, js.n_tiles,
+                                      variant_tensor_core(t.variant) && !c->h_js.literal);
         int ck2 = ckm == 1 ? ck / 2 : ck * 2;
         ck2 = std::max(kChunkAlign, ck2 / kChunkAlign * kChunkAlign);
         if (ck2 == ck) continue;
