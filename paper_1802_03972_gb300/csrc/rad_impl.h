@@ -1,8 +1,8 @@
 // Internal declarations of the radiation library (not part of the C ABI).
 //
 // Data layout in HBM, per job (one rad_ctx):
-//   om_tab   float [4][n_omega]  omega/2pi as hi part, its negation, and the
-//                                hi/lo parts of omega (rad/s) for the phase
+//   om_tab   float [3][n_omega]  omega/2pi (hi part), and 2pi times its hi and
+//                                lo parts (rad/s) for the phase's cross terms
 //   om_turns double [n_omega]    omega / 2pi (turns per second)
 //   omega    double [n_omega]
 //   dir_tab  float [12][n_dir]   n hi, n lo, transverse basis e1, e2
@@ -10,7 +10,9 @@
 //   state    float [16][n_bins]  8 compensated sums + 8 compensations:
 //                                U.e1 re/im, U.e2 re/im, V.e1 re/im, V.e2 re/im
 //   partials float [chunks][8][n_bins]   per-work-item partial sums of a call
-//   rec      float [20][n_cap]   per-particle records written by the pre-pass
+//   partials_f float [fine chunks][8][L][tile bins]  the same for the call's
+//                                fine-chunked last L tiles (TailPlan)
+//   rec      float [n_cap][20]   per-particle records written by the pre-pass
 // Bins are row-major: bin = direction * n_omega + frequency.
 #pragma once
 

@@ -28,7 +28,7 @@ def test_parity_cross_section_on_the_debug_build():
     from paper_1802_03972_gb300 import build
     lib = build.build(debug=True)
     env = dict(os.environ, RAD_LIBRARY=lib, RAD_LOG="1")
-    sel = ("all_variants or wide_warp or two_pass or changing or edge_cases or tiny_helix_mixed "
+    sel = ("all_variants or wide_warp or two_pass or changing or edge_cases or tiny_helix_mixed or fine_tail "
            "or batch_equals_standalone or graph_replay or server_results_equal or static_entry "
            "or smaller_grid or invalid_direction or two_millimetre or deterministic_and_ragged "
            "or wide_job_in_a_batch")

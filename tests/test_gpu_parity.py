@@ -143,6 +143,28 @@ def test_lwfa_full_size_sampled_rows():
         assert_parity(g[rows], ref[k], what=k)
 
 
+@pytest.mark.parametrize("n_omega, n_side, rows", [(512, 8, [5, 31, 32, 63]),
+                                                   (256, 12, [3, 79, 80, 81, 143])])
+def test_fine_tail_tiles(n_omega, n_side, rows):
+    """The fine-chunked last tiles of a job.  20480 macro-particles in 2048-particle
+    coarse chunks, 10 per tile, on 64 tiles of one direction (512 omega x 8 x 8
+    directions) or 72 tiles of two (256 omega x 12 x 12 directions, variant 9's
+    default tile at that width): on GB300 (304 resident blocks) the job fills the
+    GPU twice over, so its last 32 tiles take 40 chunks of 512 particles each and
+    keep their partial sums in the fine-tile buffer.  Directions on both sides of
+    the boundary, and both directions of the first two-direction fine tile,
+    against the oracle over all frequencies, 2 steps."""
+    wl = inputs.lwfa_bunch(n_particles=20480, n_omega=n_omega, n_side=n_side, seed=29)
+    steps = range(2)
+    ctx = gpu_run(wl, steps)
+    assert ctx.get_tile()[0] == 9
+    coh, inc, tot = ctx.spectrum()
+    bins = [(d, o) for d in rows for o in range(n_omega)]
+    ref = {k: v.reshape(len(rows), n_omega) for k, v in oracle_run(wl, steps, bins).spectra().items()}
+    for k, g in (("tot", tot), ("coh", coh), ("inc", inc)):
+        assert_parity(g[rows], ref[k], what=f"{k} rows {rows}")
+
+
 def test_lwfa_full_size_256_steps():
     """Accuracy over the workload's horizon: the full LWFA bunch for 256 of its
     2048 steps in the benchmark's launch configuration (the tuned tile), read out
