@@ -889,7 +889,9 @@ def main():
         pinned = []
         for st in steps_host[:min(ring, 8)]:
             pinned.append([torch.from_numpy(a).pin_memory() for a in (st.r, st.beta, st.beta_dot, st.w)])
-        outs = [np.zeros((wl.dirs.shape[0], wl.omega.shape[0])) for _ in range(3)]
+        # the spectra come back into pinned host buffers, as the particles go in
+        outs = [torch.zeros((wl.dirs.shape[0], wl.omega.shape[0]), dtype=torch.float64).pin_memory()
+                for _ in range(3)]
         ectx = rad.Context(wl.omega, wl.dirs, wl.ff_kind, wl.ff_width)
         if args.tile:
             ectx.set_tile(*tile)
@@ -913,7 +915,7 @@ def main():
             el = float(t.item())
         e2e = {"value": world * n_e2e * upd / el, "unit": UNIT,
                "h2d_bytes_per_step": int(sum(a.numel() * 8 for a in pinned[0])),
-               "d2h_bytes_per_step": int(sum(o.nbytes for o in outs)), "steps": n_e2e}
+               "d2h_bytes_per_step": int(sum(o.numel() * o.element_size() for o in outs)), "steps": n_e2e}
         ectx.close()
 
     # The plain FP64 GPU kernel on the same GPU (2 steps).
