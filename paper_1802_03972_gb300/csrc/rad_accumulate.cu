@@ -501,22 +501,22 @@ __device__ __forceinline__ bool process_item_fma(const JobStatic& J, const JobCa
       }
   }
 
-  // Partial sums of this work item.
+  // Partial sums of this work item.  (FP32 variants never take fine-chunked
+  // tiles, TailPlan: their items write the coarse partials directly, which
+  // keeps the fine tiles' bookkeeping out of this loop's registers.)
   const int nb = J.n_bins;
-  const PartMap pm = part_map(J, K, item, g);
-  float* part = pm.base + (size_t)chunk * pm.chunk_stride;
+  float* part = J.partials + (size_t)chunk * kComps * nb;
   if (my_d_raw < J.n_dir) {
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int o = om_first + 2 * p + e;
-        if (o < n_om && bounds_ok(chunk < item.n_chunks && part_fits(J, item, pm), J.status)) {
+        if (o < n_om && bounds_ok(chunk < J.chunk_cap && item.fine < 0, J.status)) {
           const int bin = my_d * n_om + o;
-          const size_t off = part_bin(J, item, g, my_d, o);
 #pragma unroll
           for (int c = 0; c < kComps; ++c)
-            part[(size_t)c * pm.comp_stride + off] = e ? acc2[p][c].y : acc2[p][c].x;
+            part[(size_t)c * nb + bin] = e ? acc2[p][c].y : acc2[p][c].x;
           if (LIT) {
             float* pp = J.partials_p + (size_t)chunk * 4 * nb;
 #pragma unroll
