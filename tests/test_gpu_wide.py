@@ -249,3 +249,25 @@ def test_wide_call_tiles_on_the_fp64_path(variant):
     ref = {k: v.reshape(shape) for k, v in acc.spectra().items()}
     for k, g in zip(("coh", "inc", "tot"), ctx.spectrum()):
         assert_parity(g, ref[k], what=f"variant {variant} {k}")
+
+
+def test_wide_call_with_fine_tail_tiles():
+    """A wide call whose last tiles are fine-chunked: 20480 particles over 2 mm on
+    512 omega x 8 x 8 directions, 64 tiles of 10 coarse chunks, so on GB300 (304
+    resident blocks) the last 32 tiles take 40 chunks of 512 sorted particles
+    each, rotated group by group in the wide instantiation.  Directions on both
+    sides of the boundary against the oracle over all frequencies, 2 steps."""
+    omega, dirs, r, b, bd, w = wide_bunch(20480, 1e-3, seed=61, n_omega=512, n_side=8)
+    ctx = rad.Context(omega, dirs, oracle.FF_GAUSS, 0.1e-6)
+    assert ctx.get_tile()[0] == 9
+    rows = [2, 31, 32, 63]
+    bins = [(d, o) for d in rows for o in range(omega.shape[0])]
+    bo, bdir = oracle.grid_bins(omega, dirs, bins)
+    acc = oracle.Accumulator(bo, bdir, oracle.FF_GAUSS, 0.1e-6)
+    for rr, bb, bbd, ww, t, dt in steps(r, b, bd, w, n_steps=2):
+        acc.accumulate(rr, bb, bbd, ww, t, dt)
+        ctx.accumulate(to_dev(rr), to_dev(bb), to_dev(bbd), to_dev(ww), t, dt)
+    got = dict(zip(("coh", "inc", "tot"), ctx.spectrum()))
+    ref = {k: v.reshape(len(rows), omega.shape[0]) for k, v in acc.spectra().items()}
+    for k in ("tot", "coh", "inc"):
+        assert_parity(got[k][rows], ref[k], what=f"{k} rows {rows}")
