@@ -58,7 +58,8 @@ __device__ __forceinline__ bool make_record(const JobStatic& J, const JobCall& K
     v[14] = __double2float_rn(az);
     v[15] = __double2float_rn(g2);
     v[16] = __double2float_rn(w * K.dt);
-    v[17] = __double2float_rn(sqrt(w) * K.dt);
+    // FP32 square root (the field is FP32; ~1e-7 relative): FP64's is slow on this GPU
+    v[17] = sqrtf(__double2float_rn(w)) * __double2float_rn(K.dt);
     v[18] = __double2float_rn(w - 1.0);
   } else {
 #pragma unroll
@@ -101,12 +102,15 @@ __global__ void __launch_bounds__(256) prepass_kernel(LaunchArgs a) {
   // on |n . (r - r_ref)| over the grid: |axis . dr| + sin(largest angle from
   // the axis) |dr across the axis|.
   // A call of one sorted group or less gains nothing from sorting: never wide.
+  // In FP32 on the record's (r - r_ref) / c (hi parts, seconds): the flag only
+  // steers a call to the sorted path, and a call wrongly left unsorted still
+  // runs correctly (its far tiles take the FP64 phase path).
   bool far = false;
   if (J.wide_flag && valid && !J.skip && n > kGroup && n < (1LL << 31)) {
-    const double dx = K.r[k] - rr[0], dy = K.r[n + k] - rr[1], dz = K.r[2 * n + k] - rr[2];
-    const double along = J.axis[0] * dx + J.axis[1] * dy + J.axis[2] * dz;
-    const double across = sqrt(fmax(dx * dx + dy * dy + dz * dz - along * along, 0.0));
-    far = fabs(along) + J.cone_sin * across > 0.999 * (double)J.tau_fast * kC;
+    const float along = fmaf((float)J.axis[0], v[0], fmaf((float)J.axis[1], v[1], (float)J.axis[2] * v[2]));
+    const float r2 = fmaf(v[0], v[0], fmaf(v[1], v[1], v[2] * v[2]));
+    const float across = sqrtf(fmaxf(r2 - along * along, 0.0f));
+    far = fabsf(along) + (float)J.cone_sin * across > 0.999f * J.tau_fast;
   }
   const unsigned far_lanes = __ballot_sync(__activemask(), far);
   if (far && (threadIdx.x & 31) == __ffs(far_lanes) - 1) {
