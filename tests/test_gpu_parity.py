@@ -312,3 +312,38 @@ def test_profile_clock_reports_the_kernel_sm_clock():
     assert calls == 4 and acc_ms > 0
     assert 600.0 < mhz < 2300.0, mhz
     assert ctx.profile_clock() == 0.0
+
+
+@pytest.mark.parametrize("variant", [8, 9])
+def test_compact_call_at_the_edge_of_the_fast_range(variant):
+    """A call whose particles reach 0.9 of the fast phase range from the reference
+    point (the first particle) at the highest frequency: |omega dtau| up to
+    0.9 x 2^21 turns at 1e20 rad/s, z from 0 to 35.5 um along the grid's axis.
+    There the phase's float-float cross terms are largest (variant 9 forms them
+    from TF32 splits on the tensor cores); the call is not wide, so every tile
+    stays on the fast path.  Full grid (512 log omega up to 1e20 rad/s, 4 x 4
+    directions) against the oracle, 2 steps."""
+    rng = np.random.default_rng(71)
+    n = 4000
+    z = rng.uniform(0.0, 0.9 * 2 ** 21 / (1e20 / (2 * math.pi)) * 299792458.0, n)
+    z[0] = 0.0
+    r = np.stack([rng.normal(0, 2e-6, n), rng.normal(0, 2e-6, n), z])
+    b = np.stack([rng.normal(0, 1e-3, n), rng.normal(0, 1e-3, n), np.zeros(n)])
+    b[2] = np.sqrt(1 - 1.1e-5 - b[0] ** 2 - b[1] ** 2)
+    bd = rng.normal(0, 1e13, (3, n))
+    w = rng.uniform(1e3, 1e5, n)
+    omega = inputs.omega_log(1e16, 1e20, 512)
+    dirs = inputs.dirs_grid(0.01, 4, 4)
+    bo, bdir = oracle.grid_bins(omega, dirs)
+    acc = oracle.Accumulator(bo, bdir, oracle.FF_GAUSS, 0.1e-6)
+    ctx = rad.Context(omega, dirs, oracle.FF_GAUSS, 0.1e-6)
+    ctx.set_tile(variant, 0, 0)
+    dt = 1e-16
+    for s in range(2):
+        rs = r + b * 299792458.0 * s * dt
+        acc.accumulate(rs, b, bd, w, s * dt, dt)
+        ctx.accumulate(to_dev(rs), to_dev(b), to_dev(bd), to_dev(w), s * dt, dt)
+    got = dict(zip(("coh", "inc", "tot"), ctx.spectrum()))
+    ref = {k: v.reshape(dirs.shape[0], omega.shape[0]) for k, v in acc.spectra().items()}
+    for k in ("tot", "coh", "inc"):
+        assert_parity(got[k], ref[k], what=f"variant {variant} {k}")
