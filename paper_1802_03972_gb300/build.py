@@ -9,6 +9,7 @@ when the environment variable RAD_LIBRARY names it.
 from __future__ import annotations
 
 import concurrent.futures
+import fcntl
 import os
 import shutil
 import subprocess
@@ -44,6 +45,17 @@ def _stale(target: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
     obj_dir, lib = (OBJ_DEBUG, LIB_DEBUG) if debug else (OBJ, LIB)
     os.makedirs(obj_dir, exist_ok=True)
+    # Several processes (one per rank) may call build() at once: one builds,
+    # the others wait on the lock and then find nothing stale.
+    with open(os.path.join(obj_dir, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(obj_dir, lib, force, verbose, debug)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(obj_dir: str, lib: str, force: bool, verbose: bool, debug: bool) -> str:
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     cc = nvcc()

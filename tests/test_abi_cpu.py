@@ -165,3 +165,25 @@ def test_every_header_compiles_as_pedantic_c11(tmp_path):
     r = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only",
                         "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_concurrent_build_waits_for_the_lock():
+    """One process per rank may call build() at once: a second caller waits
+    while another holds the build lock, then finds the library current."""
+    import fcntl
+    import subprocess
+    import sys
+    import time
+    from paper_1802_03972_gb300 import build
+    lib = build.build()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(build.__file__)))
+    with open(os.path.join(build.OBJ, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        child = subprocess.Popen(
+            [sys.executable, "-c", "from paper_1802_03972_gb300 import build; print(build.build())"],
+            cwd=root, stdout=subprocess.PIPE, text=True)
+        time.sleep(1.0)
+        assert child.poll() is None  # blocked on the lock
+        fcntl.flock(lock, fcntl.LOCK_UN)
+    out, _ = child.communicate(timeout=120)
+    assert child.returncode == 0 and out.strip() == lib
