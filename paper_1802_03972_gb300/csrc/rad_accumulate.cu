@@ -89,44 +89,56 @@ __device__ __forceinline__ TileGeom tile_geom(const JobStatic& J, int tile, int 
 }
 
 // A work item: its tile and particle chunk, and the chunking of that tile.
-// fine: the tile's index among the job's fine-chunked last tiles (TailPlan),
-// -1 for the others.
+// fine: the tile's index among the tiles of its fine-chunked level (TailPlan),
+// -1 for the coarse tiles.  (The level itself follows from the tile and the
+// call; the item, live across the whole particle loop, holds no more.)
 struct ItemRef {
   int tile, chunk, ck, n_chunks, fine;
 };
 
-// Item `local` of a job: the coarse tiles' items tile-major, then the fine
-// tiles' items tile-major.
+// Item `local` of a job: the coarse tiles' items tile-major, then level 0's
+// fine tiles' items, then level 1's, each tile-major.
 __device__ __forceinline__ ItemRef decode_item(const JobStatic& J, const JobCall& K,
                                                long long local) {
+  static_assert(kTailLevels == 2, "two fine levels");
   ItemRef it;
-  const long long coarse = (long long)(J.n_tiles - K.tail_tiles) * K.n_chunks;
+  const int first0 = J.n_tiles - K.tail_tiles[0] - K.tail_tiles[1];
+  const long long coarse = (long long)first0 * K.n_chunks;
+  const long long fine0 = (long long)K.tail_tiles[0] * K.n_chunks_f[0];
   if (local < coarse) {
     it.tile = (int)(local / K.n_chunks);
     it.chunk = (int)(local - (long long)it.tile * K.n_chunks);
     it.ck = K.ck;
     it.n_chunks = K.n_chunks;
     it.fine = -1;
-  } else {
+  } else if (local - coarse < fine0) {
     const long long l = local - coarse;
-    it.fine = (int)(l / K.n_chunks_f);
-    it.tile = J.n_tiles - K.tail_tiles + it.fine;
-    it.chunk = (int)(l - (long long)it.fine * K.n_chunks_f);
-    it.ck = K.ck_f;
-    it.n_chunks = K.n_chunks_f;
+    it.fine = (int)(l / K.n_chunks_f[0]);
+    it.tile = first0 + it.fine;
+    it.chunk = (int)(l - (long long)it.fine * K.n_chunks_f[0]);
+    it.ck = K.ck_f[0];
+    it.n_chunks = K.n_chunks_f[0];
+  } else {
+    const long long l = local - coarse - fine0;
+    it.fine = (int)(l / K.n_chunks_f[1]);
+    it.tile = first0 + K.tail_tiles[0] + it.fine;
+    it.chunk = (int)(l - (long long)it.fine * K.n_chunks_f[1]);
+    it.ck = K.ck_f[1];
+    it.n_chunks = K.n_chunks_f[1];
   }
   return it;
 }
 
 // Where an item's partial sums live: component comp of chunk ch at
 // base[ch * chunk_stride + comp * comp_stride + bin offset].  Coarse tiles:
-// J.partials [chunk][comp][n_bins], the offset the bin; fine tiles:
-// J.partials_f [chunk][comp][tail_tiles][NT WT], the offset the bin's index
-// within the tile.  limit: the floats from base (index checks).
+// J.partials [chunk][comp][n_bins], the offset the bin; fine tiles: their
+// level's region of J.partials_f, [chunk][comp][level tiles][NT WT], level 1's
+// after level 0's, the offset the bin's index within the tile.  room: the
+// floats from the start of the item's buffer or region.
 struct PartMap {
   float* base;
   size_t chunk_stride, comp_stride;
-  long long limit;
+  long long room;
 };
 __device__ __forceinline__ PartMap part_map(const JobStatic& J, const JobCall& K, const ItemRef& it,
                                             const TileGeom& g) {
@@ -134,12 +146,14 @@ __device__ __forceinline__ PartMap part_map(const JobStatic& J, const JobCall& K
   if (it.fine < 0) {
     m.base = J.partials;
     m.comp_stride = (size_t)J.n_bins;
-    m.limit = (long long)J.chunk_cap * kComps * J.n_bins;
+    m.room = (long long)J.chunk_cap * kComps * J.n_bins;
   } else {
-    const size_t tb = (size_t)g.NT * g.WT;
-    m.base = J.partials_f + (size_t)it.fine * tb;
-    m.comp_stride = (size_t)K.tail_tiles * tb;
-    m.limit = J.fine_cap - (long long)it.fine * (long long)tb;
+    const long long tb = (long long)g.NT * g.WT;
+    const bool l1 = it.tile >= J.n_tiles - K.tail_tiles[1];
+    const long long foff = l1 ? (long long)K.tail_tiles[0] * K.n_chunks_f[0] * kComps * tb : 0;
+    m.base = J.partials_f + foff + (long long)it.fine * tb;
+    m.comp_stride = (size_t)(l1 ? K.tail_tiles[1] : K.tail_tiles[0]) * tb;
+    m.room = J.fine_cap - foff;
   }
   m.chunk_stride = (size_t)kComps * m.comp_stride;
   return m;
@@ -182,8 +196,8 @@ __device__ __forceinline__ void discard_l2_line(const void* p) {
 // The partial sums of a tile are dead once the last arrival has added them up,
 // and every call rewrites each slot before reading it.  Dropping their L2
 // lines saves the write-back to DRAM.  Arrays: n_arrays arrays from base, one
-// every `stride` floats, each laid out as [n_bins] (fine: false) or as the
-// fine tiles' [tail_tiles][NT WT] with base at this tile (fine: true); only
+// every `stride` floats, each laid out as [n_bins] (fine: false) or as a fine
+// level's [level tiles][NT WT] with base at this tile (fine: true); only
 // whole lines inside the tile's bins of each direction are dropped, so the
 // neighbouring tiles' partials are untouched.
 template <int THREADS>
@@ -216,7 +230,7 @@ __device__ __forceinline__ void discard_tile_partials(const float* base, size_t 
 // Whether an item's chunks fit the partial-sum buffer it writes.
 __device__ __forceinline__ bool part_fits(const JobStatic& J, const ItemRef& it, const PartMap& m) {
   return it.fine < 0 ? it.n_chunks <= J.chunk_cap
-                     : J.fine_cap >= (long long)it.n_chunks * (long long)m.chunk_stride;
+                     : m.room >= (long long)it.n_chunks * (long long)m.chunk_stride;
 }
 
 template <int THREADS, bool DISCARD>
@@ -236,6 +250,10 @@ __device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall&
     float s[kComps];
 #pragma unroll
     for (int c = 0; c < kComps; ++c) s[c] = 0.0f;
+    // Unrolled so that several chunks' loads are in flight at once (a finest
+    // tail tile has over a hundred chunks, and its last arrival ends the
+    // launch); the adds keep chunk order.
+#pragma unroll 4
     for (int ch = 0; ch < it.n_chunks; ++ch) {
       const float* pc = m.base + (size_t)ch * m.chunk_stride;
 #pragma unroll

@@ -334,9 +334,7 @@ rad_status enqueue_accumulate(rad_ctx* c, long long n, const double* r, const do
   K.dt = dt;
   K.ck = ck;
   K.n_chunks = n_chunks;
-  K.tail_tiles = tail.tiles;
-  K.ck_f = tail.ck;
-  K.n_chunks_f = tail.n_chunks;
+  set_tail(K, tail);
   K.item_begin = 0;
   K.block_begin = 0;
   s = cuda_check(c, cudaMemsetAsync(c->d_counter, 0, kCounterWords * sizeof(unsigned long long),

@@ -195,9 +195,7 @@ rad_status BatchCore::run(rad_ctx* const* jobs, const rad_step* steps, int n_job
     K.dt = st.dt;
     K.ck = plan[p].ck;
     K.n_chunks = plan[p].n_chunks;
-    K.tail_tiles = plan[p].tail.tiles;
-    K.ck_f = plan[p].tail.ck;
-    K.n_chunks_f = plan[p].tail.n_chunks;
+    set_tail(K, plan[p].tail);
     K.item_begin = items;
     K.block_begin = blocks;
     K.sort_block_begin = sort_blocks;

@@ -10,8 +10,9 @@
 //   state    float [16][n_bins]  8 compensated sums + 8 compensations:
 //                                U.e1 re/im, U.e2 re/im, V.e1 re/im, V.e2 re/im
 //   partials float [chunks][8][n_bins]   per-work-item partial sums of a call
-//   partials_f float [fine chunks][8][L][tile bins]  the same for the call's
-//                                fine-chunked last L tiles (TailPlan)
+//   partials_f float  the same for the call's fine-chunked last tiles
+//                     (TailPlan): per level l, [chunks_l][8][L_l][tile bins],
+//                     level 1's region after level 0's
 //   rec      float [n_cap][20]   per-particle records written by the pre-pass
 // Bins are row-major: bin = direction * n_omega + frequency.
 #pragma once
@@ -32,6 +33,8 @@ constexpr int kOmTab = 3;
 // shared-memory tiles (threads / directions-per-tile particles) for every
 // kernel variant and tile shape.
 constexpr int kChunkAlign = 256;
+// Levels of fine-chunked last tiles (TailPlan).
+constexpr int kTailLevels = 2;
 // Automatic chunking aims at this many (coarse) work items per resident
 // block when the job's last tiles are fine-chunked (TailPlan: tensor-core
 // variants, not literal).  Each item has fixed costs (the first tile's exposed
@@ -90,8 +93,9 @@ struct JobStatic {
   const double* dirs;
   float* state;
   float* partials;                // [chunk_cap][kComps][n_bins]
-  // the fine-chunked last tiles of a call (see TailPlan):
-  // [n_chunks_f][kComps][tail_tiles][nt * wt], fine_cap floats
+  // the fine-chunked last tiles of a call (see TailPlan): per level l,
+  // [n_chunks_f[l]][kComps][tail_tiles[l]][nt * wt], level 1 after level 0;
+  // fine_cap floats
   float* partials_f;
   long long fine_cap;
   unsigned* tile_cnt;             // [n_tiles] arrival counters (self-resetting)
@@ -129,47 +133,83 @@ struct JobCall {
   long long item_begin;  // first global work item of this job
   int block_begin;       // first pre-pass block of this job
   int sort_block_begin;  // first sort-histogram block of this job
-  // the job's last tail_tiles tiles take chunks of ck_f (n_chunks_f per tile)
-  int tail_tiles;
-  int ck_f;
-  int n_chunks_f;
-  int pad_;
+  // Fine-chunked last tiles (TailPlan), level 0 then level 1 in tile order
+  // (level 1 the job's last tail_tiles[1] tiles): tail_tiles[l] tiles with
+  // chunks of ck_f[l] (n_chunks_f[l] per tile)
+  int tail_tiles[kTailLevels];
+  int ck_f[kTailLevels];
+  int n_chunks_f[kTailLevels];
 };
 
 // Finer work items for the last tiles of a job (tensor-core variants).  With
 // items of one size, the launch ends with the resident blocks finishing their
 // last items at spread-out times, about half an item idle per block.  A job
-// that fills the GPU at least twice over cuts its last L tiles into chunks of
-// a quarter of the size, L = ceil(grid / n_chunks) + 1: enough fine work for
-// every resident block to move on to it before the coarse items run out, so
-// the idle end is about half a fine item.  The plan depends on the job alone
-// (its size and tiling) and the device's resident blocks, so a job is
-// chunked alike alone, in a batch and in the server.
-struct TailPlan {
-  int tiles = 0;     // the job's last `tiles` tiles take the fine chunks
+// that fills the GPU at least twice over cuts its last L0 tiles into chunks of
+// a quarter of the size, L0 = ceil(grid / n_chunks) + 1: enough fine work for
+// every resident block to move on to it before the coarse items run out.  The
+// fine items' ends are spread in turn, over one fine item: the L1 tiles after
+// those, the job's last, take a quarter of the fine chunk, and
+// L1 = ceil(grid / n_chunks_1) + 1 from their own chunk count, about one of
+// these items per resident block, so the idle end is about half of the
+// finest item.  Each level needs a chunk at least one particle tile
+// (kChunkAlign) and smaller than the one before it, and all levels together at
+// most half the job's tiles.  The plan depends on the job alone (its size and
+// tiling) and the device's resident blocks, so a job is chunked alike alone,
+// in a batch and in the server.
+struct TailLevel {
+  int tiles = 0;     // tiles of this level
   int ck = 0;        // their chunk, a multiple of kChunkAlign
   int n_chunks = 0;  // their chunks per tile
+};
+struct TailPlan {
+  TailLevel lv[kTailLevels];
+  int tiles() const {
+    int t = 0;
+    for (int l = 0; l < kTailLevels; ++l) t += lv[l].tiles;
+    return t;
+  }
   long long items(int n_tiles, int n_chunks_coarse) const {
-    return (long long)(n_tiles - tiles) * n_chunks_coarse + (long long)tiles * n_chunks;
+    long long it = (long long)(n_tiles - tiles()) * n_chunks_coarse;
+    for (int l = 0; l < kTailLevels; ++l) it += (long long)lv[l].tiles * lv[l].n_chunks;
+    return it;
+  }
+  // floats of JobStatic::partials_f the levels before `level` take
+  long long level_offset(int level, int bins_per_tile) const {
+    long long f = 0;
+    for (int l = 0; l < level; ++l) f += (long long)lv[l].n_chunks * kComps * lv[l].tiles * bins_per_tile;
+    return f;
   }
   // floats of JobStatic::partials_f the plan needs
-  long long fine_floats(int bins_per_tile) const {
-    return (long long)n_chunks * kComps * tiles * bins_per_tile;
-  }
+  long long fine_floats(int bins_per_tile) const { return level_offset(kTailLevels, bins_per_tile); }
 };
 inline TailPlan tail_plan(bool tensor_core, long long n, int n_tiles, int ck, int n_chunks,
                           long long grid) {
   TailPlan t;
   if (!tensor_core || n <= 0 || (long long)n_tiles * n_chunks < 2 * grid) return t;
-  int ckf = (ck / 4 + kChunkAlign - 1) / kChunkAlign * kChunkAlign;
-  if (ckf < kChunkAlign) ckf = kChunkAlign;
-  if (ckf >= ck) return t;
-  const long long L = (grid + n_chunks - 1) / n_chunks + 1;
-  if (2 * L > n_tiles) return t;
-  t.tiles = (int)L;
-  t.ck = ckf;
-  t.n_chunks = (int)((n + ckf - 1) / ckf);
+  int tiles = 0;
+  for (int l = 0; l < kTailLevels; ++l) {
+    int ckf = (ck / 4 + kChunkAlign - 1) / kChunkAlign * kChunkAlign;
+    if (ckf < kChunkAlign) ckf = kChunkAlign;
+    if (ckf >= ck) break;
+    const long long ncf = (n + ckf - 1) / ckf;
+    const long long per = l == 0 ? n_chunks : ncf;  // chunks per tile L is counted in
+    const long long L = (grid + per - 1) / per + 1;
+    if (2 * (tiles + L) > n_tiles) break;
+    t.lv[l].tiles = (int)L;
+    t.lv[l].ck = ckf;
+    t.lv[l].n_chunks = (int)ncf;
+    tiles += (int)L;
+    ck = ckf;
+  }
   return t;
+}
+// The plan's fields of a call.
+inline void set_tail(JobCall& K, const TailPlan& t) {
+  for (int l = 0; l < kTailLevels; ++l) {
+    K.tail_tiles[l] = t.lv[l].tiles;
+    K.ck_f[l] = t.lv[l].ck;
+    K.n_chunks_f[l] = t.lv[l].n_chunks;
+  }
 }
 
 struct LaunchArgs {

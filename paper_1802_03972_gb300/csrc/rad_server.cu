@@ -83,12 +83,14 @@ size_t estimate_footprint(const rad_job_desc& d) {
   const size_t by_particles = nb * (size_t)((d.max_particles + kChunkAlign - 1) / kChunkAlign);
   const size_t by_items = (size_t)kItemsPerCtaUniform * resident_ctas(kDefaultVariant) * bins_per_tile + nb;
   const size_t partials = 32 * std::min(by_particles, by_items);
-  // The fine-chunked last tiles' partial sums (TailPlan): with L tiles of
-  // n_f = 4 n_c + 1 chunks, L = grid / n_c + 2 at most, L n_f <= 5 grid + 8 n_c + 2;
-  // 32 B per tile bin and (tile, chunk).
+  // The fine-chunked last tiles' partial sums (TailPlan), 32 B per tile bin
+  // and (tile, chunk).  Level 0: L0 <= grid / n_c + 2 tiles of n_0 <= 4 n_c
+  // chunks, L0 n_0 <= 4 grid + 8 n_c; level 1: L1 <= grid / n_1 + 2 tiles of
+  // n_1 <= 4 n_0 <= 16 n_c chunks, L1 n_1 <= grid + 32 n_c.  Together at most
+  // 6 grid + 40 n_c (tile, chunk) pairs, with a few to spare.
   const size_t grid = (size_t)resident_ctas(kDefaultVariant);
   const size_t tiles_per_nb = std::max<size_t>(1, nb / bins_per_tile);
-  const size_t fine = 32 * bins_per_tile * (5 * grid + 2) + 8 * partials / tiles_per_nb;
+  const size_t fine = 32 * bins_per_tile * (6 * grid + 12) + 40 * partials / tiles_per_nb;
   // Records (80 B per particle), the sort buffers of wide calls (13 B) and the
   // queued steps' staging slots (80 B each).
   return nb * (64 + 24) + partials + fine +

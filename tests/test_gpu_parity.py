@@ -143,17 +143,24 @@ def test_lwfa_full_size_sampled_rows():
         assert_parity(g[rows], ref[k], what=k)
 
 
-@pytest.mark.parametrize("n_omega, n_side, rows", [(512, 8, [5, 31, 32, 63]),
-                                                   (256, 12, [3, 79, 80, 81, 143])])
+@pytest.mark.parametrize("n_omega, n_side, rows", [
+    (512, 8, [5, 31, 32, 63]),
+    (256, 12, [3, 79, 80, 81, 143]),
+    (512, 12, [5, 106, 107, 138, 139, 143]),
+    (256, 16, [3, 181, 182, 245, 246, 247, 255]),
+])
 def test_fine_tail_tiles(n_omega, n_side, rows):
     """The fine-chunked last tiles of a job.  20480 macro-particles in 2048-particle
-    coarse chunks, 10 per tile, on 64 tiles of one direction (512 omega x 8 x 8
-    directions) or 72 tiles of two (256 omega x 12 x 12 directions, variant 9's
-    default tile at that width): on GB300 (304 resident blocks) the job fills the
-    GPU twice over, so its last 32 tiles take 40 chunks of 512 particles each and
-    keep their partial sums in the fine-tile buffer.  Directions on both sides of
-    the boundary, and both directions of the first two-direction fine tile,
-    against the oracle over all frequencies, 2 steps."""
+    coarse chunks, 10 per tile, with one direction per tile at 512 frequencies and
+    two at 256 (variant 9's default tile at that width); on GB300 (304 resident
+    blocks) each job fills the GPU twice over.  Level 0 takes 32 tiles in 40
+    chunks of 512 particles; level 1 (80 chunks of 256) follows only where its
+    5 tiles keep both levels within half the job: not on 64 tiles (8 x 8
+    directions) or 72 (12 x 12 at 256), but on 144 (12 x 12 at 512: coarse
+    directions up to 106, level 0 107-138, level 1 139-143) and 128 (16 x 16 at
+    256: coarse up to 181, level 0 182-245, level 1 246-255).  Directions on
+    both sides of each boundary, both directions of a two-direction tile, and
+    the last direction, against the oracle over all frequencies, 2 steps."""
     wl = inputs.lwfa_bunch(n_particles=20480, n_omega=n_omega, n_side=n_side, seed=29)
     steps = range(2)
     ctx = gpu_run(wl, steps)

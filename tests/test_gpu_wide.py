@@ -251,16 +251,18 @@ def test_wide_call_tiles_on_the_fp64_path(variant):
         assert_parity(g, ref[k], what=f"variant {variant} {k}")
 
 
-def test_wide_call_with_fine_tail_tiles():
+@pytest.mark.parametrize("n_side, rows", [(8, [2, 31, 32, 63]), (12, [2, 106, 107, 138, 139, 143])])
+def test_wide_call_with_fine_tail_tiles(n_side, rows):
     """A wide call whose last tiles are fine-chunked: 20480 particles over 2 mm on
-    512 omega x 8 x 8 directions, 64 tiles of 10 coarse chunks, so on GB300 (304
-    resident blocks) the last 32 tiles take 40 chunks of 512 sorted particles
-    each, rotated group by group in the wide instantiation.  Directions on both
-    sides of the boundary against the oracle over all frequencies, 2 steps."""
-    omega, dirs, r, b, bd, w = wide_bunch(20480, 1e-3, seed=61, n_omega=512, n_side=8)
+    512 omega, 10 coarse chunks per tile, so on GB300 (304 resident blocks) 32
+    tiles take 40 chunks of 512 sorted particles each, rotated group by group in
+    the wide instantiation.  On 8 x 8 directions (64 tiles) that is the last 32;
+    on 12 x 12 (144 tiles) the last 5 take a second level of 80 chunks of 256
+    particles after them.  Directions on both sides of each boundary against the
+    oracle over all frequencies, 2 steps."""
+    omega, dirs, r, b, bd, w = wide_bunch(20480, 1e-3, seed=61, n_omega=512, n_side=n_side)
     ctx = rad.Context(omega, dirs, oracle.FF_GAUSS, 0.1e-6)
     assert ctx.get_tile()[0] == 9
-    rows = [2, 31, 32, 63]
     bins = [(d, o) for d in rows for o in range(omega.shape[0])]
     bo, bdir = oracle.grid_bins(omega, dirs, bins)
     acc = oracle.Accumulator(bo, bdir, oracle.FF_GAUSS, 0.1e-6)

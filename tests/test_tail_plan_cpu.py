@@ -1,12 +1,15 @@
-"""The fine-chunked tail plan (rad_impl.h: TailPlan, tail_plan) on the host: a
-job that fills the GPU at least twice over cuts its last L = ceil(grid /
-n_chunks) + 1 tiles into chunks of a quarter of the size, enough fine work for
-every resident block to move on to it before the coarse items run out; small
-jobs, FP32 variants and plans that would cover half the tiles or more are left
-alone.  The plan is compiled from the library's own header with the host
-compiler and checked against these rules and one worked case (the LWFA
-workload: 1e5 particles, 256 tiles of 512 bins, 10 coarse chunks of 10752 on
-304 resident blocks)."""
+"""The fine-chunked tail plan (rad_impl.h: TailPlan, tail_plan) on the host.
+A job that fills the GPU at least twice over cuts its last tiles finer, in two
+levels: L0 = ceil(grid / n_chunks) + 1 tiles in chunks of a quarter of the
+coarse chunk, enough fine work for every resident block to move on to it
+before the coarse items run out, then the job's last L1 = ceil(grid / n1) + 1
+tiles in chunks of a quarter of that (n1 chunks per tile), about one of these
+items per block.  Small jobs, FP32 variants, chunks that cannot shrink below
+one particle tile and plans that would cover half the tiles or more are left
+alone (level 1 alone may drop out).  The plan is compiled from the library's
+own header with the host compiler and checked against these rules and one
+worked case (the LWFA workload: 1e5 particles, 256 tiles of 512 bins, 10
+coarse chunks of 10752 on 304 resident blocks)."""
 import math
 import os
 import shutil
@@ -50,23 +53,33 @@ def plan(tmp_path_factory):
 
 
 def expected(tc, n, n_tiles, ck, nc, grid):
-    """The plan's rules restated."""
+    """The plan's rules restated: ((L0, ck0, n0), (L1, ck1, n1))."""
+    none = (0, 0, 0)
     if not tc or n <= 0 or n_tiles * nc < 2 * grid:
-        return 0, 0, 0
-    ckf = max(ALIGN, math.ceil(ck // 4 / ALIGN) * ALIGN)
-    if ckf >= ck:
-        return 0, 0, 0
-    L = math.ceil(grid / nc) + 1
-    if 2 * L > n_tiles:
-        return 0, 0, 0
-    return L, ckf, math.ceil(n / ckf)
+        return none, none
+    levels, tiles = [], 0
+    for level in range(2):
+        ckf = max(ALIGN, math.ceil(ck // 4 / ALIGN) * ALIGN)
+        if ckf >= ck:
+            break
+        ncf = math.ceil(n / ckf)
+        L = math.ceil(grid / (nc if level == 0 else ncf)) + 1
+        if 2 * (tiles + L) > n_tiles:
+            break
+        levels.append((L, ckf, ncf))
+        tiles += L
+        ck = ckf
+    levels += [none] * (2 - len(levels))
+    return tuple(levels)
 
 
 def test_lwfa_workload_worked_case(plan):
-    (tiles, ckf, ncf, items, fine), = plan([(1, 100000, 256, 10752, 10, 304, 512)])
-    assert (tiles, ckf, ncf) == (32, 2816, 36)
-    assert items == 224 * 10 + 32 * 36
-    assert fine == 36 * 8 * 32 * 512
+    (t0, ck0, n0, t1, ck1, n1, items, fine, off1), = plan([(1, 100000, 256, 10752, 10, 304, 512)])
+    assert (t0, ck0, n0) == (32, 2816, 36)
+    assert (t1, ck1, n1) == (4, 768, 131)   # ceil(1e5 / 768) = 131, ceil(304 / 131) + 1 = 4
+    assert items == 220 * 10 + 32 * 36 + 4 * 131
+    assert off1 == 36 * 8 * 32 * 512
+    assert fine == off1 + 131 * 8 * 4 * 512
 
 
 def test_plan_follows_its_rules(plan):
@@ -81,16 +94,28 @@ def test_plan_follows_its_rules(plan):
                         cases.append((tc, n, n_tiles, ck, nc_real, grid, 512))
     got = plan(cases)
     assert len(got) == len(cases)
-    for c, (tiles, ckf, ncf, items, fine) in zip(cases, got):
+    n_two = 0
+    for c, (t0, ck0, n0, t1, ck1, n1, items, fine, off1) in zip(cases, got):
         tc, n, n_tiles, ck, nc, grid, bpt = c
-        assert (tiles, ckf, ncf) == expected(tc, n, n_tiles, ck, nc, grid), c
-        assert items == (n_tiles - tiles) * nc + tiles * ncf, c
-        assert fine == ncf * 8 * tiles * bpt, c
-        if tiles:
-            assert ckf % ALIGN == 0 and ckf < ck, c
-            assert tiles * nc >= grid, c          # fine work covers one coarse item per block
-            assert 2 * tiles <= n_tiles, c
+        assert ((t0, ck0, n0), (t1, ck1, n1)) == expected(tc, n, n_tiles, ck, nc, grid), c
+        assert items == (n_tiles - t0 - t1) * nc + t0 * n0 + t1 * n1, c
+        assert off1 == n0 * 8 * t0 * bpt, c
+        assert fine == off1 + n1 * 8 * t1 * bpt, c
+        assert t0 or not t1, c                   # level 1 only after level 0
+        prev = ck
+        for tiles, ckf, ncf, cover in ((t0, ck0, n0, nc), (t1, ck1, n1, None)):
+            if not tiles:
+                continue
+            assert ckf % ALIGN == 0 and ckf < prev, c
             assert (ncf - 1) * ckf < n <= ncf * ckf, c
+            # level 0's work covers one coarse item per block, level 1 one of its own
+            assert tiles * (cover or ncf) >= grid, c
+            prev = ckf
+        assert 2 * (t0 + t1) <= n_tiles, c
+        # the serving engine's footprint bound on (tile, chunk) pairs
+        assert t0 * n0 + t1 * n1 <= 6 * grid + 40 * nc + 12, c
+        n_two += t1 > 0
+    assert n_two > 20  # both levels are exercised
 
 
 def test_plan_is_off_where_it_cannot_help(plan):
@@ -101,3 +126,13 @@ def test_plan_is_off_where_it_cannot_help(plan):
         (1, 1000, 4096, 256, 4, 304, 512),       # chunks already at the minimum
     ])
     assert [g[0] for g in got] == [0, 0, 0, 0]
+    assert [g[3] for g in got] == [0, 0, 0, 0]
+
+
+def test_second_level_needs_room(plan):
+    # level 0 only: its chunk is one particle tile already (1024 / 4 = 256)
+    (g,) = plan([(1, 100000, 256, 1024, 98, 304, 512)])
+    assert g[:3] == (5, 256, 391) and g[3] == 0
+    # level 0 only: level 1 would take the job past half its tiles
+    (g,) = plan([(1, 100000, 70, 10752, 10, 304, 512)])
+    assert g[0] == 32 and g[3] == 0
