@@ -97,15 +97,17 @@ struct ItemRef {
 };
 
 // Item `local` of a job: the coarse tiles' items tile-major, then level 0's
-// fine tiles' items, then level 1's, each tile-major.
+// fine tiles' items, then level 1's, each tile-major.  FINE = false: the
+// FP32 variants, whose jobs are never fine-chunked (every item coarse).
+template <bool FINE>
 __device__ __forceinline__ ItemRef decode_item(const JobStatic& J, const JobCall& K,
                                                long long local) {
   static_assert(kTailLevels == 2, "two fine levels");
   ItemRef it;
-  const int first0 = J.n_tiles - K.tail_tiles[0] - K.tail_tiles[1];
+  const int first0 = FINE ? J.n_tiles - K.tail_tiles[0] - K.tail_tiles[1] : J.n_tiles;
   const long long coarse = (long long)first0 * K.n_chunks;
   const long long fine0 = (long long)K.tail_tiles[0] * K.n_chunks_f[0];
-  if (local < coarse) {
+  if (!FINE || local < coarse) {
     it.tile = (int)(local / K.n_chunks);
     it.chunk = (int)(local - (long long)it.tile * K.n_chunks);
     it.ck = K.ck;
@@ -929,7 +931,7 @@ __global__ void __launch_bounds__(THREADS, MINB) accumulate_kernel(LaunchArgs a)
     const JobCall K = a.use_inline ? a.inline_call : a.jc[j];
     // Tile-major order: the chunks of one tile run close together in time, so
     // their partial sums are still in L2 when the tile's last arrival reads them.
-    const ItemRef it = decode_item(J, K, item - K.item_begin);
+    const ItemRef it = decode_item<TC>(J, K, item - K.item_begin);
     bool ok;
     if constexpr (TC)
       ok = process_item_tc<THREADS, PASSES, 2 * W, WIDE, XT>(J, K, it, smem, &bar, phase, &s_flag);
