@@ -235,6 +235,71 @@ __device__ __forceinline__ bool part_fits(const JobStatic& J, const ItemRef& it,
                      : m.room >= (long long)it.n_chunks * (long long)m.chunk_stride;
 }
 
+// Rotation of a bin's chunk sums by e^{i omega tau_ref(n)} (psi in turns).
+__device__ __forceinline__ void bin_rotation(const JobStatic& J, int d, int o, float& cp, float& sp) {
+  const double* nd = J.dirs + 3 * d;
+  const double tref = J.ref[3] - (nd[0] * J.ref[0] + nd[1] * J.ref[1] + nd[2] * J.ref[2]) * kInvC;
+  double psi = J.om_turns[o] * tref;
+  psi -= rint(psi);
+  sincospif(2.0f * (float)psi, &sp, &cp);
+}
+
+// A fine tile's last arrival (TailPlan).  Its bins are contiguous in its
+// level's region ([chunk][comp][level tiles][NT WT], NT WT a multiple of 4,
+// 16-byte aligned), so the chunk sums are read four bins at a time: a unit is
+// (bin quad, component pair), consecutive threads take consecutive quads, and
+// each thread sums two units at once, keeping many loads in flight (a finest
+// tile has over a hundred chunks, and the last of these sums ends the
+// launch).  Every bin's components are still added in chunk order.
+template <int THREADS>
+__device__ __forceinline__ void fine_tile_sums(const JobStatic& J, const TileGeom& g, const PartMap& m,
+                                               int n_chunks) {
+  const int n_quads = g.NT * g.WT / 4, n_units = 4 * n_quads;
+  const int nb = J.n_bins, n_om = J.n_omega;
+  for (int ua = threadIdx.x; ua < n_units; ua += 2 * THREADS) {
+    const int ub = min(ua + THREADS, n_units - 1);  // a repeat of ua's last unit when past the end
+    const bool has_b = ua + THREADS < n_units;
+    const int pa = ua / n_quads, qa = ua - pa * n_quads;
+    const int pb = ub / n_quads, qb = ub - pb * n_quads;
+    const float* ra = m.base + (size_t)(2 * pa) * m.comp_stride + 4 * qa;
+    const float* rb = m.base + (size_t)(2 * pb) * m.comp_stride + 4 * qb;
+    float4 are = make_float4(0.f, 0.f, 0.f, 0.f), aim = are, bre = are, bim = are;
+#pragma unroll 4
+    for (int ch = 0; ch < n_chunks; ++ch) {
+      const size_t co = (size_t)ch * m.chunk_stride;
+      const float4 x0 = __ldcg(reinterpret_cast<const float4*>(ra + co));
+      const float4 x1 = __ldcg(reinterpret_cast<const float4*>(ra + co + m.comp_stride));
+      const float4 y0 = __ldcg(reinterpret_cast<const float4*>(rb + co));
+      const float4 y1 = __ldcg(reinterpret_cast<const float4*>(rb + co + m.comp_stride));
+      are.x += x0.x; are.y += x0.y; are.z += x0.z; are.w += x0.w;
+      aim.x += x1.x; aim.y += x1.y; aim.z += x1.z; aim.w += x1.w;
+      bre.x += y0.x; bre.y += y0.y; bre.z += y0.z; bre.w += y0.w;
+      bim.x += y1.x; bim.y += y1.y; bim.z += y1.z; bim.w += y1.w;
+    }
+    float* st = J.state;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !has_b) break;
+      const int p = h ? pb : pa, q = h ? qb : qa;
+      const float re4[4] = {h ? bre.x : are.x, h ? bre.y : are.y, h ? bre.z : are.z, h ? bre.w : are.w};
+      const float im4[4] = {h ? bim.x : aim.x, h ? bim.y : aim.y, h ? bim.z : aim.z, h ? bim.w : aim.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = 4 * q + k, dl = i / g.WT;
+        const int d = g.d0 + dl, o = g.o0 + (i - dl * g.WT);
+        if (d >= J.n_dir || o >= n_om) continue;
+        const int bin = d * n_om + o, c = 2 * p;
+        float cp, sp;
+        bin_rotation(J, d, o, cp, sp);
+        const float re = re4[k] * cp - im4[k] * sp;
+        const float im = re4[k] * sp + im4[k] * cp;
+        kahan_add(&st[(size_t)c * nb + bin], &st[(size_t)(kComps + c) * nb + bin], re);
+        kahan_add(&st[(size_t)(c + 1) * nb + bin], &st[(size_t)(kComps + c + 1) * nb + bin], im);
+      }
+    }
+  }
+}
+
 template <int THREADS, bool DISCARD>
 __device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall& K,
                                               const ItemRef& it) {
@@ -243,7 +308,10 @@ __device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall&
   const PartMap m = part_map(J, K, it, g);
   const int nb = J.n_bins, n_om = J.n_omega;
   if (!bounds_ok(part_fits(J, it, m) && tile < J.n_tiles, J.status)) return;
-  for (int i = threadIdx.x; i < g.NT * g.WT; i += THREADS) {
+  // (literal contexts run an FP32 variant: never fine tiles)
+  const bool vec = it.fine >= 0 && !J.literal && ((g.NT * g.WT) & 3) == 0;
+  if (vec) fine_tile_sums<THREADS>(J, g, m, it.n_chunks);
+  for (int i = threadIdx.x; i < (vec ? 0 : g.NT * g.WT); i += THREADS) {
     const int dl = i / g.WT;
     const int d = g.d0 + dl, o = g.o0 + (i - dl * g.WT);
     if (d >= J.n_dir || o >= n_om) continue;
@@ -252,21 +320,15 @@ __device__ __forceinline__ void tile_epilogue(const JobStatic& J, const JobCall&
     float s[kComps];
 #pragma unroll
     for (int c = 0; c < kComps; ++c) s[c] = 0.0f;
-    // Unrolled so that several chunks' loads are in flight at once (a finest
-    // tail tile has over a hundred chunks, and its last arrival ends the
-    // launch); the adds keep chunk order.
+    // (unrolled so that several chunks' loads are in flight; the adds keep chunk order)
 #pragma unroll 4
     for (int ch = 0; ch < it.n_chunks; ++ch) {
       const float* pc = m.base + (size_t)ch * m.chunk_stride;
 #pragma unroll
       for (int c = 0; c < kComps; ++c) s[c] += __ldcg(&pc[(size_t)c * m.comp_stride + off]);
     }
-    const double* nd = J.dirs + 3 * d;
-    const double tref = J.ref[3] - (nd[0] * J.ref[0] + nd[1] * J.ref[1] + nd[2] * J.ref[2]) * kInvC;
-    double psi = J.om_turns[o] * tref;
-    psi -= rint(psi);
     float sp, cp;
-    sincospif(2.0f * (float)psi, &sp, &cp);
+    bin_rotation(J, d, o, cp, sp);
     float* st = J.state;
 #pragma unroll
     for (int c = 0; c < kComps; c += 2) {
